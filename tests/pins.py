@@ -1,0 +1,282 @@
+"""Checks that tie the oracle to mathematics outside itself.
+
+Each function raises AssertionError when the oracle disagrees with the fact
+it states.  ``test_oracle_pins.py`` runs them against the oracle;
+``test_oracle_mutants.py`` runs them against copies of the oracle with
+planted mistakes and requires that some check fails for every mutant.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+import fe_inputs as fi
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_paper_example():
+    with open(os.path.join(GOLDEN, "paper_csr_example.json")) as f:
+        g = json.load(f)
+    A1 = fi.CSR(np.array(g["IA"], dtype=np.int32), np.array(g["JA"], dtype=np.int32),
+                np.array(g["AA"], dtype=np.float64), 5, index_base=1)
+    A0 = fi.CSR(A1.row_ptr - 1, A1.col_idx - 1, A1.val.copy(), 5, 0)
+    return g, A1, A0
+
+
+def pin_spmv_paper_example():
+    """Sec. 2.3 worked example: exact integer products, 1-based and 0-based CSR."""
+    g, A1, A0 = load_paper_example()
+    for p in g["products"]:
+        x = np.array(p["x"], dtype=np.float64)
+        assert np.array_equal(oracle.spmv(A1, x), np.array(p["Ax"], dtype=np.float64))
+        assert np.array_equal(oracle.spmv(A0, x), np.array(p["Ax"], dtype=np.float64))
+    # The CSR arrays describe the printed dense matrix.
+    assert np.array_equal(A1.to_dense(), np.array(g["dense"], dtype=np.float64))
+
+
+def pin_spmv_dense_bruteforce(seed: int = 3):
+    """Irregular CSR (empty rows, rows longer than 32) against a dense product."""
+    for s in range(seed, seed + 3):
+        A = fi.random_csr(60, s, 0, 12, empty_frac=0.2, long_rows=(45, 70), ncols=80)
+        A.n = 60
+        x = fi.uniform(s, 9, 80)
+        D = np.zeros((60, 80))
+        for i in range(60):
+            for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                D[i, A.col_idx[k]] += A.val[k]
+        y = oracle.spmv(A, x)
+        ref = D @ x
+        scale = np.abs(D) @ np.abs(x)
+        assert np.all(np.abs(y - ref) <= 1e-14 * np.maximum(scale, 1e-300))
+        # integer-valued matrix and vector: every partial sum is exact
+        Ai = fi.random_csr(60, s + 100, 0, 40, empty_frac=0.1, integer=True)
+        xi = np.round(fi.uniform(s, 10, 60, -9, 9))
+        Di = Ai.to_dense()
+        assert np.array_equal(oracle.spmv(Ai, xi), Di @ xi)
+
+
+def laplace7_eigpair(N: int, j: int, k: int, l: int):
+    idx = np.arange(1, N + 1)
+    th = np.pi / (N + 1)
+    sx, sy, sz = np.sin(j * th * idx), np.sin(k * th * idx), np.sin(l * th * idx)
+    v = (sz[:, None, None] * sy[None, :, None] * sx[None, None, :]).ravel()
+    lam = sum(4.0 * math.sin(m * math.pi / (2 * (N + 1))) ** 2 for m in (j, k, l))
+    return v, lam
+
+
+def pin_laplace7_eigenpairs(N: int = 9):
+    """A v = lambda v for the sine modes of the 7-point operator (closed form)."""
+    A = fi.laplace7(N)
+    for (j, k, l) in [(1, 1, 1), (N, N, N), (1, 2, 3), (4, 1, 7), (2, 9, 5)]:
+        v, lam = laplace7_eigpair(N, j, k, l)
+        Av = oracle.spmv(A, v)
+        assert np.linalg.norm(Av - lam * v) <= 1e-13 * lam * np.linalg.norm(v)
+
+
+def q1_eigpair(N: int, j: int, k: int, l: int):
+    v, _ = laplace7_eigpair(N, j, k, l)
+    h = 1.0 / (N + 1)
+
+    def km(m):
+        c = math.cos(m * math.pi / (N + 1))
+        return 2.0 - 2.0 * c, (4.0 + 2.0 * c) / 6.0
+
+    (kj, mj), (kk, mk), (kl, ml) = km(j), km(k), km(l)
+    return v, h * (kj * mk * ml + mj * kk * ml + mj * mk * kl)
+
+
+def pin_q1_eigenpairs(N: int = 7):
+    """Constant-density Q1 operator: sine modes with lambda = h(k m m + m k m + m m k)."""
+    A = fi.q1(N, sigma=0.0, seed=0)
+    for (j, k, l) in [(1, 1, 1), (N, N, N), (2, 3, 1), (6, 1, 4)]:
+        v, lam = q1_eigpair(N, j, k, l)
+        Av = oracle.spmv(A, v)
+        assert np.linalg.norm(Av - lam * v) <= 1e-12 * lam * np.linalg.norm(v)
+
+
+def pin_blas1(seed: int = 5):
+    """dot against an exactly rounded sum; axpy and ewmul elementwise."""
+    n = 1001
+    x, y = fi.uniform(seed, 1, n), fi.uniform(seed, 2, n)
+    exact = math.fsum(float(a) * float(b) for a, b in zip(x, y))  # products are rounded, sum exact
+    d = oracle.dot(x, y)
+    assert abs(d - exact) <= n * 2.0 ** -53 * float(np.sum(np.abs(x * y))) * 2
+    xi, yi = np.round(x * 1000), np.round(y * 1000)
+    assert oracle.dot(xi, yi) == float(np.sum(xi.astype(np.int64) * yi.astype(np.int64)))
+    assert oracle.dot(x[:0], y[:0]) == 0.0
+    a = 0.37
+    assert np.array_equal(oracle.axpy(a, xi, yi), a * xi + yi)
+    assert np.array_equal(oracle.axpy(2.0, xi, yi), 2.0 * xi + yi)
+    assert np.array_equal(oracle.ewmul(x, y), x * y)
+
+
+def pin_cg_finite_termination():
+    """Tiny SPD systems: CG reaches 1e-10 in at most n (+2 rounding slack) steps
+    and matches a dense direct solve."""
+    for s, n in [(1, 5), (2, 12), (3, 20)]:
+        A = fi.random_spd(n, s, density=0.5)
+        D = A.to_dense()
+        xs = fi.uniform(s, 7, n)
+        b = D @ xs
+        r = oracle.cg(A, b, tol=1e-10, maxit=n + 2)
+        assert r.status == oracle.OK
+        assert r.iters <= n + 2
+        xd = np.linalg.solve(D, b)
+        assert np.linalg.norm(r.x - xd) <= 1e-8 * np.linalg.norm(xd)
+        assert r.relres_true <= 1e-9
+
+
+def pin_cg_monotone_error(N: int = 6):
+    """||x_k - x*||_A and ||x_k - x*||_2 decrease monotonically (Hestenes-Stiefel)."""
+    A = fi.q1(N, sigma=1.0, seed=11)
+    D = A.to_dense()
+    xs = fi.xstar(11, A.n)
+    b = D @ xs
+    full = oracle.cg(A, b, tol=1e-10, maxit=10 * A.n)
+    assert full.status == oracle.OK
+    prev_a, prev_2 = math.inf, math.inf
+    for k in range(0, full.iters + 1):
+        xk = oracle.cg(A, b, force_iters=k).x
+        e = xk - xs
+        ea, e2 = math.sqrt(e @ D @ e), np.linalg.norm(e)
+        assert ea <= prev_a * (1 + 1e-12) + 1e-13
+        assert e2 <= prev_2 * (1 + 1e-12) + 1e-13
+        prev_a, prev_2 = ea, e2
+
+
+def pin_cg_laplace_bounds(N: int = 16):
+    """7-point operator with closed-form kappa: Chebyshev residual bound, the
+    iteration count it implies, Lanczos extreme Ritz values, and the error of
+    the manufactured solution."""
+    A = fi.laplace7(N)
+    lmin = 3 * 4.0 * math.sin(math.pi / (2 * (N + 1))) ** 2
+    lmax = 3 * 4.0 * math.sin(N * math.pi / (2 * (N + 1))) ** 2
+    kappa = lmax / lmin
+    xs = fi.xstar(0, A.n)
+    b = oracle.spmv(A, xs)
+    r = oracle.cg(A, b, tol=1e-10, maxit=A.n, history=True)
+    assert r.status == oracle.OK and r.relres_true <= 1.5e-10
+    c = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    for k, rk in enumerate(r.res):
+        assert rk / r.res[0] <= 2 * math.sqrt(kappa) * c ** k * (1 + 1e-9)
+    kmax = math.ceil(math.log(1e-10 / (2 * math.sqrt(kappa))) / math.log(c))
+    assert r.iters <= kmax
+    # Lanczos tridiagonal from the CG coefficients (Saad, Sec. 6.7.3)
+    k = r.iters
+    al, be = r.alpha, r.beta
+    T = np.zeros((k, k))
+    for i in range(k):
+        T[i, i] = 1.0 / al[i] + (be[i - 1] / al[i - 1] if i > 0 else 0.0)
+        if i + 1 < k:
+            T[i, i + 1] = T[i + 1, i] = math.sqrt(be[i]) / al[i]
+    ev = np.linalg.eigvalsh(T)
+    assert abs(ev[0] - lmin) <= 1e-6 * lmin
+    assert abs(ev[-1] - lmax) <= 1e-6 * lmax
+    err = np.linalg.norm(r.x - xs) / np.linalg.norm(xs)
+    assert err <= kappa * r.relres_true * 1.01
+
+
+def pin_cg_orthogonality():
+    """Residuals of early steps are mutually orthogonal."""
+    A = fi.q1(5, sigma=1.0, seed=4)
+    xs = fi.xstar(4, A.n)
+    b = oracle.spmv(A, xs)
+    rs = []
+    for k in range(6):
+        xk = oracle.cg(A, b, force_iters=k).x
+        rs.append(b - oracle.spmv(A, xk))
+    for i in range(6):
+        for j in range(i):
+            c = abs(rs[i] @ rs[j]) / (np.linalg.norm(rs[i]) * np.linalg.norm(rs[j]))
+            assert c <= 1e-8, (i, j, c)
+
+
+def pin_cg_special_cases():
+    """b = 0; maxit reached; an indefinite matrix; a nonzero initial guess."""
+    A = fi.laplace7(4)
+    r = oracle.cg(A, np.zeros(A.n))
+    assert r.status == oracle.OK and r.iters == 0 and np.all(r.x == 0)
+    b = oracle.spmv(A, fi.xstar(1, A.n))
+    r = oracle.cg(A, b, tol=1e-14, maxit=2)
+    assert r.status == oracle.NOTCONV and r.iters == 2
+    Ind = fi.dense_to_csr(np.diag([1.0, -1.0]))
+    r = oracle.cg(Ind, np.array([1.0, 1.0]))
+    assert r.status == oracle.BREAKDOWN
+    xs = fi.xstar(2, A.n)
+    b = oracle.spmv(A, xs)
+    r = oracle.cg(A, b, tol=1e-12, maxit=A.n, x0=xs)   # exact guess: no step needed
+    assert r.iters == 0 and r.relres_true <= 1e-15
+
+
+def pin_mixed_cg():
+    """Mixed precision reaches the FP64 true residual 1e-10 and the solution
+    agrees with a dense solve; its FP32 product matches the FP64 product to
+    FP32 rounding."""
+    A = fi.q1(8, sigma=1.0, seed=21)
+    D = A.to_dense()
+    xs = fi.xstar(21, A.n)
+    b = D @ xs
+    r = oracle.cg_mixed(A, b, tol=1e-10, replace_every=20)
+    assert r.status == oracle.OK, r
+    assert r.relres_true <= 1e-10
+    xd = np.linalg.solve(D, b)
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(r.x - xd) <= kappa * 1e-10 * np.linalg.norm(xd) * 2
+    v32 = A.val.astype(np.float32)
+    x32 = xs.astype(np.float32)
+    y32 = oracle.spmv_f32(A, v32, x32).astype(np.float64)
+    ref = np.abs(D) @ np.abs(xs)
+    assert np.all(np.abs(y32 - D @ xs) <= 40 * 2.0 ** -24 * ref)
+
+
+def pin_matrix_stats(golden_table1=True):
+    """Table 1 column definitions: the 5x5 example by hand and the paper's own
+    density and nz/h columns recomputed from its h and nz."""
+    g, A1, A0 = load_paper_example()
+    st = oracle.matrix_stats(A1)
+    for key, v in g["stats"].items():
+        assert abs(st[key] - v) <= 1e-12, (key, st[key], v)
+    with open(os.path.join(GOLDEN, "paper_table1.json")) as f:
+        t1 = json.load(f)
+    for row in t1["rows"][1:3]:  # row 0 holds a misprinted nz/h (see the fixture's reading)
+        h, nz = int(row[0]), int(row[1])
+        lens = np.full(h, nz // h, dtype=np.int64)
+        lens[: nz % h] += 1
+        rp = np.zeros(h + 1, dtype=np.int64)
+        rp[1:] = np.cumsum(lens)
+        ci = np.zeros(nz, dtype=np.int32)  # columns do not enter density or nz/h
+        A = fi.CSR(rp.astype(np.int32), ci, np.zeros(nz), h)
+        s = oracle.matrix_stats(A)
+        assert round(100.0 * s["density"], 3) == row[2]
+        assert round(s["nz_per_h"], 3) == row[5]
+    # Stencil matrices: bandwidth, max_row and nz in closed form.
+    N = 5
+    s7 = oracle.matrix_stats(fi.laplace7(N))
+    assert s7["bandwidth"] == N * N and s7["max_row"] == 7 and s7["nz"] == 7 * N**3 - 6 * N**2
+    sq = oracle.matrix_stats(fi.q1(N, 1.0, 0))
+    assert sq["bandwidth"] == N * N + N + 1 and sq["max_row"] == 27 and sq["nz"] == (3 * N - 2) ** 3
+    # row lengths of the Q1 pattern: 27 inside, fewer next to the boundary
+    lens = np.where((np.arange(N) > 0) & (np.arange(N) < N - 1), 3, 2)
+    L = (lens[:, None, None] * lens[None, :, None] * lens[None, None, :]).ravel()
+    assert abs(sq["nz_per_h_stddev"] - float(np.std(L))) <= 1e-12
+
+
+ALL_PINS = [
+    pin_spmv_paper_example,
+    pin_spmv_dense_bruteforce,
+    pin_laplace7_eigenpairs,
+    pin_q1_eigenpairs,
+    pin_blas1,
+    pin_cg_finite_termination,
+    pin_cg_monotone_error,
+    pin_cg_laplace_bounds,
+    pin_cg_orthogonality,
+    pin_cg_special_cases,
+    pin_mixed_cg,
+    pin_matrix_stats,
+]
