@@ -1,0 +1,264 @@
+"""ctypes binding of ``libcg.so`` (the C ABI in ``include/cg.h``).
+
+Argument marshalling only: every operation runs in the library's CUDA
+kernels.  Tensors are torch tensors (CUDA for device arguments; CPU tensors
+or numpy arrays where the C ABI accepts host memory).  If the library has not
+been built this module raises at import: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcg.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOTCONV, CG_EBREAKDOWN, CG_ETIMEOUT, CG_EBUSY = range(8)
+STATUS_NAMES = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_ENOTCONV",
+                5: "CG_EBREAKDOWN", 6: "CG_ETIMEOUT", 7: "CG_EBUSY"}
+CG_PREC_FP64, CG_PREC_MIXED = 0, 1
+
+
+class CGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cg_csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("index_base", ctypes.c_int32), ("on_device", ctypes.c_int32)]
+
+
+class cg_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("replace_every", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("wait_limit_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcg.so is not built ({LIB_PATH}); run paper_2112_10823_gb300.build.build() "
+                          "(nvcc for sm_103a) first: there is no non-CUDA fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    lib.cg_opts_default.restype = None
+    lib.cg_opts_default.argtypes = [P(cg_opts)]
+    lib.cg_create.restype = ctypes.c_int
+    lib.cg_create.argtypes = [P(vp), P(cg_csr), i64, i64, P(cg_opts)]
+    lib.cg_destroy.restype = ctypes.c_int
+    lib.cg_destroy.argtypes = [vp]
+    lib.cg_last_error.restype = ctypes.c_char_p
+    lib.cg_last_error.argtypes = [vp]
+    lib.cg_info.restype = ctypes.c_int
+    lib.cg_info.argtypes = [vp, P(i64), P(i64), P(i32)]
+    lib.cg_spmv.restype = ctypes.c_int
+    lib.cg_spmv.argtypes = [vp, vp, vp]
+    lib.cg_dot.restype = ctypes.c_int
+    lib.cg_dot.argtypes = [vp, i64, vp, vp, vp]
+    lib.cg_axpy.restype = ctypes.c_int
+    lib.cg_axpy.argtypes = [vp, i64, dbl, vp, vp]
+    lib.cg_ewmul.restype = ctypes.c_int
+    lib.cg_ewmul.argtypes = [vp, i64, vp, vp, vp]
+    lib.cg_solve.restype = ctypes.c_int
+    lib.cg_solve.argtypes = [vp, vp, vp, dbl, i64, P(i64), P(dbl)]
+    lib.cg_selftest_wait_timeout.restype = ctypes.c_int
+    lib.cg_selftest_wait_timeout.argtypes = [i32, P(i32)]
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (None -> 0)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    if hasattr(a, "ctypes"):
+        return int(a.ctypes.data)
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"expected a tensor, an array or an address, got {type(a)}")
+
+
+def _is_cuda(a) -> bool:
+    return bool(getattr(a, "is_cuda", False))
+
+
+def _check(status: int, handle=None) -> int:
+    if status != CG_OK:
+        raise CGError(status, lib.cg_last_error(handle).decode(errors="replace"))
+    return status
+
+
+def _check_f64(name, t, n=None, cuda=True):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cuda and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+
+
+@dataclass
+class SolveResult:
+    status: int
+    iters: int
+    relres: float
+
+    @property
+    def ok(self) -> bool:
+        return self.status == CG_OK
+
+
+class Handle:
+    """A matrix resident on the GPU (wraps ``cg_handle``)."""
+
+    def __init__(self, ptr: int, n: int, nnz: int, stream: int):
+        self._h = ctypes.c_void_p(ptr)
+        self.n, self.nnz, self.stream = n, nnz, stream
+
+    @property
+    def value(self):
+        return self._h.value
+
+    @property
+    def nblocks(self) -> int:
+        nb = ctypes.c_int32(0)
+        _check(lib.cg_info(self._h, None, None, ctypes.byref(nb)), self._h)
+        return nb.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib.cg_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+def cg_create(row_ptr, col_idx, val, n: int | None = None, nnz: int | None = None, index_base: int = 0,
+              stream=None, device: int | None = None, precision: int = CG_PREC_FP64,
+              replace_every: int = 50, validate: bool = True, wait_limit_ms: int = 2000) -> Handle:
+    """cg_create: copy a CSR matrix (IA/JA/AA; host or CUDA arrays) to the GPU.
+
+    ``stream``: a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int, or None for
+    torch's current stream on ``device``.
+    """
+    import numpy as np
+    import torch
+    n = int(row_ptr.shape[0]) - 1 if n is None else int(n)
+    nnz = int(col_idx.shape[0]) if nnz is None else int(nnz)
+    on_dev = _is_cuda(row_ptr)
+    if on_dev != _is_cuda(col_idx) or on_dev != _is_cuda(val):
+        raise ValueError("row_ptr, col_idx and val must all be host or all be CUDA")
+    for name, a, dt in (("row_ptr", row_ptr, "int32"), ("col_idx", col_idx, "int32"), ("val", val, "float64")):
+        if isinstance(a, torch.Tensor):
+            if str(a.dtype) != f"torch.{dt}" or not a.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous {dt} tensor")
+        elif isinstance(a, np.ndarray):
+            if a.dtype != np.dtype(dt) or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError(f"{name} must be a C-contiguous {dt} array")
+        else:
+            raise TypeError(f"{name} must be a torch tensor or a numpy array")
+    if device is None:
+        device = row_ptr.device.index if on_dev else (torch.cuda.current_device() if torch.cuda.is_available() else -1)
+    if stream is None and torch.cuda.is_available() and device is not None and device >= 0:
+        stream = torch.cuda.current_stream(device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (int(stream) if stream else 0)
+    csr = cg_csr(_ptr(row_ptr), _ptr(col_idx), _ptr(val), int(index_base), 1 if on_dev else 0)
+    o = cg_opts()
+    lib.cg_opts_default(ctypes.byref(o))
+    o.stream = s
+    o.device = -1 if device is None else int(device)
+    o.precision = int(precision)
+    o.replace_every = int(replace_every)
+    o.validate = 1 if validate else 0
+    o.wait_limit_ms = int(wait_limit_ms)
+    out = ctypes.c_void_p(0)
+    _check(lib.cg_create(ctypes.byref(out), ctypes.byref(csr), n, nnz, ctypes.byref(o)))
+    return Handle(out.value, n, nnz, s)
+
+
+def cg_destroy(h: Handle) -> None:
+    h.close()
+
+
+def cg_spmv(h: Handle, x, y) -> None:
+    """y = A x (CUDA float64 tensors of n elements)."""
+    _check_f64("x", x, h.n)
+    _check_f64("y", y, h.n)
+    _check(lib.cg_spmv(h._h, _ptr(x), _ptr(y)), h._h)
+
+
+def cg_dot(h: Handle, x, y, out, n: int | None = None) -> None:
+    """out[0] = x . y (CUDA float64 tensors; out has at least one element)."""
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    _check_f64("out", out, 1)
+    _check(lib.cg_dot(h._h, n, _ptr(x), _ptr(y), _ptr(out)), h._h)
+
+
+def cg_axpy(h: Handle, a: float, x, y, n: int | None = None) -> None:
+    """y <- a x + y."""
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    _check(lib.cg_axpy(h._h, n, float(a), _ptr(x), _ptr(y)), h._h)
+
+
+def cg_ewmul(h: Handle, x, y, z, n: int | None = None) -> None:
+    """z = x * y element-wise."""
+    n = x.numel() if n is None else int(n)
+    for nm, t in (("x", x), ("y", y), ("z", z)):
+        _check_f64(nm, t, n)
+    _check(lib.cg_ewmul(h._h, n, _ptr(x), _ptr(y), _ptr(z)), h._h)
+
+
+def cg_solve(h: Handle, b, x, tol: float = 1e-10, maxit: int | None = None, raise_on_error: bool = False
+             ) -> SolveResult:
+    """Solve A x = b; b and x are CUDA tensors, CPU tensors or numpy arrays
+    (float64, n elements; x holds the initial guess and receives the solution)."""
+    maxit = 10 * h.n if maxit is None else int(maxit)
+    for nm, t in (("b", b), ("x", x)):
+        if hasattr(t, "dtype") and str(t.dtype) not in ("torch.float64", "float64"):
+            raise TypeError(f"{nm} must be float64")
+        if (t.numel() if hasattr(t, "numel") else t.size) < h.n:
+            raise ValueError(f"{nm} is shorter than n")
+    it = ctypes.c_int64(0)
+    rr = ctypes.c_double(0.0)
+    st = lib.cg_solve(h._h, _ptr(b), _ptr(x), float(tol), maxit, ctypes.byref(it), ctypes.byref(rr))
+    if st not in (CG_OK, CG_ENOTCONV, CG_EBREAKDOWN) or (raise_on_error and st != CG_OK):
+        _check(st, h._h)
+    return SolveResult(st, it.value, rr.value)
+
+
+def cg_selftest_wait_timeout(limit_ms: int = 200) -> int:
+    """Run the bounded-wait self-test; returns the status the kernel reported."""
+    ks = ctypes.c_int32(-1)
+    _check(lib.cg_selftest_wait_timeout(int(limit_ms), ctypes.byref(ks)))
+    return ks.value
+
+
+def last_error(h: Handle | None = None) -> str:
+    return lib.cg_last_error(h._h if h is not None else None).decode(errors="replace")

@@ -1,0 +1,151 @@
+// Vector kernels benchmarked by the paper (Sec. 5.2): dot product, addition
+// of vectors (y <- a x + y) and element-wise product (z = x o y).  All three
+// stream HBM; the dot product is deterministic for a given length (fixed grid,
+// fixed per-thread order, fixed combine order).
+#include "cg_device.cuh"
+
+namespace cgk {
+
+// Grid of the dot kernel: enough CTAs to fill the GPU for long vectors, no
+// more than needed for short ones.  Depends only on n and the SM count.
+int dot_grid(int64_t n, int num_sms) {
+  const int64_t per_cta = static_cast<int64_t>(kBlock) * 8;
+  int64_t g = (n + per_cta - 1) / per_cta;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 4;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+// Each thread sums x_i y_i over i = t, t + T, t + 2T, ... (T = threads in the
+// grid, four independent accumulators combined in a fixed order), the CTA sums
+// its threads, and the last CTA to finish adds the CTA partials in CTA order
+// and resets the arrival counter for the next call.
+__global__ void __launch_bounds__(kBlock) dot_kernel(int64_t n, const double* __restrict__ x,
+                                                     const double* __restrict__ y, double* __restrict__ out,
+                                                     double* __restrict__ partials, unsigned int* counter) {
+  __shared__ double red[kBlock + 4];
+  __shared__ unsigned int is_last;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+  int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (; i + 3 * T < n; i += 4 * T) {
+    a0 = fma(x[i], y[i], a0);
+    a1 = fma(x[i + T], y[i + T], a1);
+    a2 = fma(x[i + 2 * T], y[i + 2 * T], a2);
+    a3 = fma(x[i + 3 * T], y[i + 3 * T], a3);
+  }
+  for (; i < n; i += T) a0 = fma(x[i], y[i], a0);
+  double s = block_sum((a0 + a1) + (a2 + a3), red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    double t = 0.0;
+    for (int j = threadIdx.x; j < static_cast<int>(gridDim.x); j += kBlock) t += __ldcg(partials + j);
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *counter = 0u;
+    }
+  }
+}
+
+cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partials,
+                       unsigned int* counter, int grid, cudaStream_t s) {
+  dot_kernel<<<grid, kBlock, 0, s>>>(n, x, y, out, partials, counter);
+  return cudaGetLastError();
+}
+
+namespace {
+inline int stream_grid(int64_t n) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n / 2 + kBlock - 1) / kBlock;
+  const int64_t cap = static_cast<int64_t>(sms) * 8;
+  int64_t g = want < cap ? want : cap;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+}  // namespace
+
+// y <- a x + y.  Pairs of elements move as 16-byte loads/stores when both
+// vectors are 16-byte aligned; otherwise element by element.
+template <bool kVec>
+__global__ void __launch_bounds__(kBlock) axpy_kernel(int64_t n, double a, const double* __restrict__ x,
+                                                      double* __restrict__ y) {
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+  int64_t t = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  if constexpr (kVec) {
+    const int64_t n2 = n / 2;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    double2* y2 = reinterpret_cast<double2*>(y);
+    for (int64_t i = t; i < n2; i += T) {
+      const double2 xv = x2[i];
+      double2 yv = y2[i];
+      yv.x = fma(a, xv.x, yv.x);
+      yv.y = fma(a, xv.y, yv.y);
+      y2[i] = yv;
+    }
+    if (t == 0 && (n & 1)) y[n - 1] = fma(a, x[n - 1], y[n - 1]);
+  } else {
+    for (int64_t i = t; i < n; i += T) y[i] = fma(a, x[i], y[i]);
+  }
+}
+
+template <bool kVec>
+__global__ void __launch_bounds__(kBlock) ewmul_kernel(int64_t n, const double* x, const double* y,
+                                                       double* z) {  // z may alias x or y
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+  int64_t t = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  if constexpr (kVec) {
+    const int64_t n2 = n / 2;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    const double2* y2 = reinterpret_cast<const double2*>(y);
+    double2* z2 = reinterpret_cast<double2*>(z);
+    for (int64_t i = t; i < n2; i += T) {
+      const double2 xv = x2[i], yv = y2[i];
+      z2[i] = make_double2(xv.x * yv.x, xv.y * yv.y);
+    }
+    if (t == 0 && (n & 1)) z[n - 1] = x[n - 1] * y[n - 1];
+  } else {
+    for (int64_t i = t; i < n; i += T) z[i] = x[i] * y[i];
+  }
+}
+
+cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+  const int g = stream_grid(n);
+  if (aligned16(x) && aligned16(y)) axpy_kernel<true><<<g, kBlock, 0, s>>>(n, a, x, y);
+  else axpy_kernel<false><<<g, kBlock, 0, s>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ewmul(int64_t n, const double* x, const double* y, double* z, cudaStream_t s) {
+  const int g = stream_grid(n);
+  if (aligned16(x) && aligned16(y) && aligned16(z)) ewmul_kernel<true><<<g, kBlock, 0, s>>>(n, x, y, z);
+  else ewmul_kernel<false><<<g, kBlock, 0, s>>>(n, x, y, z);
+  return cudaGetLastError();
+}
+
+}  // namespace cgk
+
+namespace cgk {
+
+// FP32 copy of the matrix values (mixed-precision handles), round to nearest.
+__global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < n; i += T)
+    dst[i] = __double2float_rn(src[i]);
+}
+
+cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s) {
+  f64_to_f32_kernel<<<stream_grid(n), kBlock, 0, s>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace cgk

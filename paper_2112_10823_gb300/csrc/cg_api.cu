@@ -1,0 +1,485 @@
+// Host side of the C ABI declared in include/cg.h: argument checks, CSR
+// validation and upload, the row partition of the persistent kernels, device
+// memory ownership, and the launch + read-back of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cg.h"
+#include "cg_internal.h"
+
+namespace cgk {
+cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
+}
+
+struct cg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = CG_PREC_FP64;
+  int replace_every = 50;
+  unsigned long long wait_limit_ns = 2000000000ull;
+  int64_t n = 0, nnz = 0;
+  int num_sms = 0;
+  int nblocks = 0;
+  int nchunks = 0;
+  // device memory owned by the handle
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val = nullptr;
+  float* d_val32 = nullptr;
+  int32_t* d_chunk_row = nullptr;
+  int32_t* d_chunk_mode = nullptr;
+  int32_t* d_block_chunk = nullptr;
+  double* d_r = nullptr;
+  double* d_p = nullptr;
+  double* d_q = nullptr;
+  float* d_p32 = nullptr;
+  double* d_xbuf = nullptr;   // staging of host x
+  double* d_bbuf = nullptr;   // staging of host b
+  double* d_partials = nullptr;
+  cgk::SolveCtrl* d_ctrl = nullptr;
+  double* d_dot_partials = nullptr;
+  unsigned int* d_dot_counter = nullptr;
+  int32_t* d_err = nullptr;
+  cgk::SolveCtrl* h_ctrl = nullptr;  // pinned
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(cg_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(cg_ctx* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA, m);
+}
+
+template <typename T>
+cudaError_t dalloc(cg_ctx* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count ? count * sizeof(T) : 16);
+  if (e == cudaSuccess) {
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+void release(cg_ctx* h) {
+  if (!h) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  h->h_ctrl = nullptr;
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Row partition of the persistent kernels.  Rows are split into `nblocks`
+// contiguous ranges of about equal cost (stored entries + kRowCost per row,
+// the per-row vector work), and each range into chunks of at most kChunkRows
+// rows and kChunkNnz entries.  A row longer than kChunkNnz is a chunk alone.
+constexpr int64_t kRowCost = 6;
+
+void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, std::vector<int32_t>& chunk_row,
+                     std::vector<int32_t>& chunk_mode, std::vector<int32_t>& block_chunk) {
+  chunk_row.clear();
+  chunk_mode.clear();
+  block_chunk.assign(static_cast<size_t>(nblocks) + 1, 0);
+  const int64_t total = static_cast<int64_t>(rp[n]) + kRowCost * n;
+  int64_t row = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    block_chunk[b] = static_cast<int32_t>(chunk_row.size());
+    // end of this block's range: first row i with cost(0, i) >= total * (b+1) / nblocks
+    const int64_t goal = (b == nblocks - 1) ? total : (total * (b + 1)) / nblocks;
+    int64_t lo = row, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (static_cast<int64_t>(rp[mid]) + kRowCost * mid >= goal) hi = mid;
+      else lo = mid + 1;
+    }
+    const int64_t end = (b == nblocks - 1) ? n : lo;
+    while (row < end) {
+      const int64_t len0 = rp[row + 1] - rp[row];
+      if (len0 > cgk::kChunkNnz) {
+        chunk_row.push_back(static_cast<int32_t>(row));
+        chunk_mode.push_back(cgk::kBlockPerRow);
+        ++row;
+        continue;
+      }
+      const int64_t start = row;
+      int64_t cnt = 0, maxlen = 0;
+      while (row < end && row - start < cgk::kChunkRows) {
+        const int64_t len = rp[row + 1] - rp[row];
+        if (len > cgk::kChunkNnz || cnt + len > cgk::kChunkNnz) break;
+        cnt += len;
+        if (len > maxlen) maxlen = len;
+        ++row;
+      }
+      const int64_t rows = row - start;
+      const bool warp = (cnt > 48 * rows) || maxlen > 256;
+      chunk_row.push_back(static_cast<int32_t>(start));
+      chunk_mode.push_back(warp ? cgk::kWarpPerRow : cgk::kThreadPerRow);
+    }
+  }
+  block_chunk[nblocks] = static_cast<int32_t>(chunk_row.size());
+  chunk_row.push_back(static_cast<int32_t>(n));
+}
+
+cgk::DevCsr dev_view(const cg_ctx* h) {
+  cgk::DevCsr A;
+  A.row_ptr = h->d_row_ptr;
+  A.col_idx = h->d_col;
+  A.val = h->d_val;
+  A.val32 = h->d_val32;
+  A.chunk_row = h->d_chunk_row;
+  A.chunk_mode = h->d_chunk_mode;
+  A.block_chunk = h->d_block_chunk;
+  A.n = static_cast<int32_t>(h->n);
+  A.nchunks = h->nchunks;
+  A.nblocks = h->nblocks;
+  A.nnz = h->nnz;
+  return A;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void cg_opts_default(cg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->stream = nullptr;
+  o->device = -1;
+  o->precision = CG_PREC_FP64;
+  o->replace_every = 50;
+  o->validate = 1;
+  o->wait_limit_ms = 2000;
+}
+
+const char* cg_last_error(cg_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const cg_opts* opts) {
+  if (!out) return fail(nullptr, CG_EINVAL, "cg_create: out is NULL");
+  *out = nullptr;
+  if (!csr) return fail(nullptr, CG_EINVAL, "cg_create: csr is NULL");
+  cg_opts o;
+  cg_opts_default(&o);
+  if (opts) o = *opts;
+  const int base = csr->index_base;
+  if (base != 0 && base != 1) return fail(nullptr, CG_EINVAL, "cg_create: index_base must be 0 or 1");
+  const int64_t kMaxIdx = 2147483647LL - 16;
+  if (n < 0 || nnz < 0 || n > kMaxIdx || nnz > kMaxIdx)
+    return fail(nullptr, CG_EINVAL, "cg_create: n and nnz must be in [0, 2^31 - 16)");
+  if (o.precision != CG_PREC_FP64 && o.precision != CG_PREC_MIXED)
+    return fail(nullptr, CG_EINVAL, "cg_create: unknown precision");
+  if (o.replace_every < 0) return fail(nullptr, CG_EINVAL, "cg_create: replace_every must be >= 0");
+  if (!csr->row_ptr || (nnz > 0 && (!csr->col_idx || !csr->val)))
+    return fail(nullptr, CG_EINVAL, "cg_create: NULL CSR array");
+
+  // Host copies of row_ptr and col_idx (needed for validation and partitioning).
+  std::vector<int32_t> rp(static_cast<size_t>(n) + 1), ci;
+  const bool need_cols_on_host = o.validate || base != 0 || !csr->on_device;
+  if (!csr->on_device) {
+    std::memcpy(rp.data(), csr->row_ptr, sizeof(int32_t) * (n + 1));
+    ci.assign(csr->col_idx, csr->col_idx + nnz);
+  }
+
+  // Host inputs are validated before any CUDA call (see the block below).
+  auto validate_csr = [&](std::string& bad) {
+    bad.clear();
+    if (rp[0] != base) bad = "row_ptr[0] != index_base";
+    for (int64_t i = 0; bad.empty() && i < n; ++i)
+      if (rp[i + 1] < rp[i]) bad = "row_ptr decreases at row " + std::to_string(i);
+    if (bad.empty() && static_cast<int64_t>(rp[n]) - base != nnz) bad = "row_ptr[n] != nnz + index_base";
+    for (int64_t k = 0; bad.empty() && k < nnz; ++k)
+      if (ci[k] < base || static_cast<int64_t>(ci[k]) - base >= n)
+        bad = "column index out of range at entry " + std::to_string(k);
+    return bad.empty();
+  };
+  if (!csr->on_device && o.validate) {
+    std::string bad;
+    if (!validate_csr(bad)) return fail(nullptr, CG_EINVAL, "cg_create: invalid CSR: " + bad);
+  }
+
+  cg_ctx* h = new (std::nothrow) cg_ctx();
+  if (!h) return fail(nullptr, CG_ENOMEM, "cg_create: host allocation failed");
+  if (o.device >= 0) h->device = o.device;
+  else if (cudaGetDevice(&h->device) != cudaSuccess) h->device = 0;
+  DeviceGuard guard(h->device);
+  h->stream = static_cast<cudaStream_t>(o.stream);
+  h->precision = o.precision;
+  h->replace_every = o.replace_every;
+  h->wait_limit_ns = static_cast<unsigned long long>(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
+  h->n = n;
+  h->nnz = nnz;
+  cudaError_t e;
+#define CG_TRY(call, what)                       \
+  do {                                           \
+    e = (call);                                  \
+    if (e != cudaSuccess) {                      \
+      int rc__ = cuda_fail(nullptr, e, what);    \
+      release(h);                                \
+      delete h;                                  \
+      return rc__;                               \
+    }                                            \
+  } while (0)
+
+  if (csr->on_device) {
+    CG_TRY(cudaMemcpy(rp.data(), csr->row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost),
+           "cg_create: copy of row_ptr");
+    if (need_cols_on_host && nnz > 0) {
+      ci.resize(static_cast<size_t>(nnz));
+      CG_TRY(cudaMemcpy(ci.data(), csr->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost),
+             "cg_create: copy of col_idx");
+    }
+  }
+  // Validation of the CSR structure (Sec. 2.3 definition) for device inputs.
+  if (csr->on_device && o.validate) {
+    std::string bad;
+    if (!validate_csr(bad)) {
+      delete h;
+      return fail(nullptr, CG_EINVAL, "cg_create: invalid CSR: " + bad);
+    }
+  }
+  if (base) {
+    for (auto& v : rp) v -= 1;
+    for (auto& v : ci) v -= 1;
+  }
+
+  int sms = 0;
+  CG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "cg_create: SM count");
+  h->num_sms = sms;
+  const int per_sm = cgk::solve_blocks_per_sm(o.precision == CG_PREC_MIXED);
+  if (per_sm <= 0) {
+    int rc = fail(nullptr, CG_ECUDA, "cg_create: the solve kernel cannot be resident (occupancy 0)");
+    release(h);
+    delete h;
+    return rc;
+  }
+  h->nblocks = sms * per_sm;
+
+  std::vector<int32_t> chunk_row, chunk_mode, block_chunk;
+  build_partition(rp, n, h->nblocks, chunk_row, chunk_mode, block_chunk);
+  h->nchunks = static_cast<int>(chunk_mode.size());
+
+  const size_t pad = cgk::kPadEntries;
+  CG_TRY(dalloc(h, &h->d_row_ptr, n + 1), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_col, nnz + pad), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_val, nnz + pad), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_chunk_row, chunk_row.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_chunk_mode, chunk_mode.size() + 1), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_block_chunk, block_chunk.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_r, n), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_p, n), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_q, n), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_xbuf, n), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_bbuf, n), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_partials, static_cast<size_t>(4) * h->nblocks), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_ctrl, 1), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_dot_partials, static_cast<size_t>(4) * sms + 8), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_dot_counter, 4), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_err, 4), "cg_create: cudaMalloc");
+  if (o.precision == CG_PREC_MIXED) {
+    CG_TRY(dalloc(h, &h->d_val32, nnz + pad), "cg_create: cudaMalloc");
+    CG_TRY(dalloc(h, &h->d_p32, n), "cg_create: cudaMalloc");
+  }
+  CG_TRY(cudaMallocHost(&h->h_ctrl, sizeof(cgk::SolveCtrl)), "cg_create: cudaMallocHost");
+
+  CG_TRY(cudaMemcpy(h->d_row_ptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "cg_create: upload");
+  CG_TRY(cudaMemset(h->d_col, 0, sizeof(int32_t) * (nnz + pad)), "cg_create: memset");
+  CG_TRY(cudaMemset(h->d_val, 0, sizeof(double) * (nnz + pad)), "cg_create: memset");
+  if (nnz > 0) {
+    if (!ci.empty())
+      CG_TRY(cudaMemcpy(h->d_col, ci.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice), "cg_create: upload");
+    else
+      CG_TRY(cudaMemcpy(h->d_col, csr->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice),
+             "cg_create: upload");
+    CG_TRY(cudaMemcpy(h->d_val, csr->val, sizeof(double) * nnz,
+                      csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice),
+           "cg_create: upload");
+  }
+  CG_TRY(cudaMemcpy(h->d_chunk_row, chunk_row.data(), sizeof(int32_t) * chunk_row.size(), cudaMemcpyHostToDevice),
+         "cg_create: upload");
+  if (!chunk_mode.empty())
+    CG_TRY(cudaMemcpy(h->d_chunk_mode, chunk_mode.data(), sizeof(int32_t) * chunk_mode.size(),
+                      cudaMemcpyHostToDevice),
+           "cg_create: upload");
+  CG_TRY(cudaMemcpy(h->d_block_chunk, block_chunk.data(), sizeof(int32_t) * block_chunk.size(),
+                    cudaMemcpyHostToDevice),
+         "cg_create: upload");
+  CG_TRY(cudaMemset(h->d_dot_counter, 0, 16), "cg_create: memset");
+  CG_TRY(cudaMemset(h->d_err, 0, 16), "cg_create: memset");
+  if (o.precision == CG_PREC_MIXED) {
+    CG_TRY(cudaMemset(h->d_val32, 0, sizeof(float) * (nnz + pad)), "cg_create: memset");
+    if (nnz > 0) CG_TRY(cgk::launch_f64_to_f32(nnz, h->d_val, h->d_val32, nullptr), "cg_create: FP32 copy");
+  }
+  CG_TRY(cudaDeviceSynchronize(), "cg_create: synchronize");
+#undef CG_TRY
+  *out = h;
+  return CG_OK;
+}
+
+int cg_destroy(cg_handle h) {
+  if (!h) return CG_OK;
+  release(h);
+  delete h;
+  return CG_OK;
+}
+
+int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_info: NULL handle");
+  if (n) *n = h->n;
+  if (nnz) *nnz = h->nnz;
+  if (nblocks) *nblocks = h->nblocks;
+  return CG_OK;
+}
+
+int cg_spmv(cg_handle h, const double* x, double* y) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_spmv: NULL handle");
+  if (h->n == 0) return CG_OK;
+  if (!x || !y) return fail(h, CG_EINVAL, "cg_spmv: NULL vector");
+  DeviceGuard g(h->device);
+  cudaError_t e = cgk::launch_spmv(dev_view(h), x, y, h->d_err, h->stream);
+  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_spmv: launch");
+}
+
+int cg_dot(cg_handle h, int64_t n, const double* x, const double* y, double* result) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_dot: NULL handle");
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_dot: bad arguments");
+  DeviceGuard g(h->device);
+  const int grid = cgk::dot_grid(n, h->num_sms);
+  cudaError_t e = cgk::launch_dot(n, x, y, result, h->d_dot_partials, h->d_dot_counter, grid, h->stream);
+  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_dot: launch");
+}
+
+int cg_axpy(cg_handle h, int64_t n, double a, const double* x, double* y) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_axpy: NULL handle");
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_axpy: bad arguments");
+  if (n == 0) return CG_OK;
+  DeviceGuard g(h->device);
+  cudaError_t e = cgk::launch_axpy(n, a, x, y, h->stream);
+  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_axpy: launch");
+}
+
+int cg_ewmul(cg_handle h, int64_t n, const double* x, const double* y, double* z) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_ewmul: NULL handle");
+  if (n < 0 || (n > 0 && (!x || !y || !z))) return fail(h, CG_EINVAL, "cg_ewmul: bad arguments");
+  if (n == 0) return CG_OK;
+  DeviceGuard g(h->device);
+  cudaError_t e = cgk::launch_ewmul(n, x, y, z, h->stream);
+  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_ewmul: launch");
+}
+
+int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit, int64_t* iters, double* relres) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_solve: NULL handle");
+  if (!iters || !relres) return fail(h, CG_EINVAL, "cg_solve: NULL output");
+  if (!(tol >= 0.0)) return fail(h, CG_EINVAL, "cg_solve: tol must be >= 0");
+  if (maxit < 0) return fail(h, CG_EINVAL, "cg_solve: maxit must be >= 0");
+  *iters = 0;
+  *relres = 0.0;
+  if (h->n == 0) return CG_OK;
+  if (!b || !x) return fail(h, CG_EINVAL, "cg_solve: NULL vector");
+  DeviceGuard g(h->device);
+  const size_t bytes = sizeof(double) * static_cast<size_t>(h->n);
+  const bool b_dev = is_device_ptr(b), x_dev = is_device_ptr(x);
+  const double* db = b;
+  double* dx = x;
+  cudaError_t e;
+  if (!b_dev) {
+    e = cudaMemcpyAsync(h->d_bbuf, b, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: copy of b");
+    db = h->d_bbuf;
+  }
+  if (!x_dev) {
+    e = cudaMemcpyAsync(h->d_xbuf, x, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: copy of x");
+    dx = h->d_xbuf;
+  }
+  e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(cgk::SolveCtrl), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: memset");
+  cgk::SolveParams P;
+  P.A = dev_view(h);
+  P.b = db;
+  P.x = dx;
+  P.r = h->d_r;
+  P.p = h->d_p;
+  P.q = h->d_q;
+  P.p32 = h->d_p32;
+  P.partials = h->d_partials;
+  P.ctrl = h->d_ctrl;
+  P.tol = tol;
+  P.maxit = maxit;
+  P.replace_every = h->replace_every;
+  P.wait_limit_ns = h->wait_limit_ns;
+  e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: cooperative launch");
+  e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(cgk::SolveCtrl), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: read-back");
+  if (!x_dev) {
+    e = cudaMemcpyAsync(x, h->d_xbuf, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: copy of x");
+  }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: synchronize");
+  *iters = h->h_ctrl->iters;
+  *relres = h->h_ctrl->relres_true;
+  const int st = h->h_ctrl->status;
+  if (st == CG_ETIMEOUT)
+    return fail(h, CG_ETIMEOUT, "cg_solve: a device-side wait gave up (site " +
+                                    std::to_string(h->h_ctrl->timeout_site) + ")");
+  if (st == CG_EBREAKDOWN) return fail(h, CG_EBREAKDOWN, "cg_solve: breakdown (p.Ap <= 0 or not finite)");
+  if (st == CG_ENOTCONV) return fail(h, CG_ENOTCONV, "cg_solve: maxit reached before the tolerance");
+  return st;
+}
+
+int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status) {
+  if (!kernel_status || limit_ms <= 0 || limit_ms > 10000)
+    return fail(nullptr, CG_EINVAL, "cg_selftest_wait_timeout: limit_ms in (0, 10000] and a status pointer");
+  cgk::SolveCtrl* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(cgk::SolveCtrl));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_selftest_wait_timeout: cudaMalloc");
+  cgk::SolveCtrl hc;
+  e = cudaMemset(d, 0, sizeof(cgk::SolveCtrl));
+  if (e == cudaSuccess)
+    e = cgk::launch_wait_timeout_selftest(d, static_cast<unsigned long long>(limit_ms) * 1000000ull, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&hc, d, sizeof(hc), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_selftest_wait_timeout");
+  *kernel_status = hc.status;
+  return CG_OK;
+}
+
+}  // extern "C"

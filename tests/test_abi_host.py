@@ -1,0 +1,104 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+include/cg.h declares, and rejects malformed input before touching CUDA."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cg.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2112_10823_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s*(cg_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["cg_create", "cg_destroy", "cg_spmv", "cg_dot", "cg_axpy", "cg_ewmul", "cg_solve",
+                     "cg_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(cg_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    import ctypes
+    lib = ctypes.CDLL(built)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_header_compiles_as_c(tmp_path):
+    c = tmp_path / "t.c"
+    c.write_text('#include "cg.h"\nint main(void){cg_opts o; cg_opts_default(&o); return o.validate == 1 ? 0 : 1;}\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", f"-I{os.path.dirname(HEADER)}", str(c)],
+                   check=True)
+
+
+def _bad(kind):
+    A = fi.laplace7(3)
+    rp, ci, va = A.row_ptr.copy(), A.col_idx.copy(), A.val.copy()
+    if kind == "col_range":
+        ci[4] = A.n
+    elif kind == "col_negative":
+        ci[0] = -1
+    elif kind == "row_ptr_decreasing":
+        rp[5], rp[6] = rp[6], rp[5]
+    elif kind == "row_ptr_start":
+        rp = rp + 1
+    elif kind == "nnz_mismatch":
+        rp[-1] -= 1
+    return rp, ci, va, A.n
+
+
+@pytest.mark.parametrize("kind", ["col_range", "col_negative", "row_ptr_decreasing", "row_ptr_start",
+                                  "nnz_mismatch"])
+def test_malformed_csr_rejected_without_gpu(built, kind):
+    import paper_2112_10823_gb300 as cg
+    rp, ci, va, n = _bad(kind)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(rp, ci, va, n=n, nnz=len(ci))
+    assert e.value.status == cg.CG_EINVAL
+    assert "invalid CSR" in str(e.value)
+
+
+def test_bad_arguments_rejected(built):
+    import paper_2112_10823_gb300 as cg
+    A = fi.laplace7(2)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.row_ptr, A.col_idx, A.val, index_base=2)
+    assert e.value.status == cg.CG_EINVAL
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.row_ptr, A.col_idx, A.val, precision=7)
+    assert e.value.status == cg.CG_EINVAL
+    # one-based input validated as one-based
+    B = fi.to_one_based(A)
+    with pytest.raises(cg.CGError):
+        cg.cg_create(B.row_ptr, B.col_idx, B.val, index_base=0)
+
+
+def test_no_gpu_fails_loudly(built):
+    """Without a usable GPU a valid matrix is refused with CG_ECUDA: there is no CPU path."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2112_10823_gb300 as cg
+    A = fi.laplace7(3)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.row_ptr, A.col_idx, A.val)
+    assert e.value.status in (cg.CG_ECUDA, cg.CG_ENOMEM)

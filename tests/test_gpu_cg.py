@@ -1,0 +1,212 @@
+"""CG solves on the GPU against the oracle (through the C ABI).
+
+Stopping iterations may differ by rounding of the sums close to the
+threshold, so the iterates are compared at the GPU's iteration count: the
+oracle is rerun for exactly that many steps and the two solutions must agree
+to 1e-8 relative.  The GPU's true residual must be <= 1e-10 and its solution
+within kappa * relres of the manufactured one.
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+import oracle
+from gpu_util import cg_mod, handle, iters_close, kappa_estimate
+
+pytestmark = pytest.mark.gpu
+
+
+def solve(h, b, x0=None, tol=1e-10, maxit=None):
+    import torch
+    cg = cg_mod()
+    bd = torch.as_tensor(b, dtype=torch.float64).cuda()
+    xd = torch.zeros_like(bd) if x0 is None else torch.as_tensor(x0, dtype=torch.float64).cuda().clone()
+    res = cg.cg_solve(h, bd, xd, tol=tol, maxit=maxit)
+    return res, xd.cpu().numpy()
+
+
+def check_against_oracle(A, b, res, x, xs=None, tol=1e-10, maxit=None, x0=None):
+    cg = cg_mod()
+    ref = oracle.cg(A, b, tol=tol, maxit=maxit if maxit is not None else 10 * A.n, x0=x0)
+    assert res.status == cg.CG_OK, (res, cg.last_error())
+    assert ref.status == oracle.OK
+    assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    assert res.relres <= tol
+    same = oracle.cg(A, b, force_iters=res.iters, x0=x0)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= tol * 1.0000001
+    assert abs(true_rel - res.relres) <= 1e-3 * true_rel + 1e-16
+    if xs is not None:
+        kap = kappa_estimate(A, b)
+        assert np.linalg.norm(x - xs) <= 1.01 * kap * res.relres * np.linalg.norm(xs)
+    return ref
+
+
+def test_laplace7_n16():
+    """7-point Laplacian on a 16^3 grid (n = 4096), x* ~ U(-1,1), b = A x*."""
+    A = fi.laplace7(16)
+    xs = fi.xstar(0, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    check_against_oracle(A, b, res, x, xs)
+
+
+@pytest.mark.parametrize("N,seed", [(24, 1), (10, 2), (3, 3)])
+def test_q1_small(N, seed):
+    A = fi.q1(N, 1.0, seed)
+    xs = fi.xstar(seed, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    check_against_oracle(A, b, res, x, xs)
+
+
+def test_q1_n64_full():
+    """The 64^3 Q1 workload with lognormal density: the bench's configuration."""
+    A = fi.q1(64, 1.0, 0)
+    xs = fi.xstar(0, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    check_against_oracle(A, b, res, x)
+
+
+def test_q1_n160_properties():
+    """The 160^3 workload (4.1M rows, 109M entries): too large for an oracle
+    solve; the oracle recomputes the true residual of the GPU's x instead."""
+    import torch
+    A = fi.q1(160, 1.0, 0)
+    xs = fi.xstar(0, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=20000)
+    assert res.status == cg_mod().CG_OK, res
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 * 1.0000001
+    assert abs(true_rel - res.relres) <= 1e-3 * true_rel
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-4
+    del A
+    torch.cuda.empty_cache()
+
+
+def test_nonzero_initial_guess():
+    A = fi.q1(12, 1.0, 4)
+    xs = fi.xstar(4, A.n)
+    b = oracle.spmv(A, xs)
+    x0 = fi.uniform(4, 99, A.n)
+    with handle(A) as h:
+        res, x = solve(h, b, x0=x0, maxit=10 * A.n)
+    check_against_oracle(A, b, res, x, x0=x0)
+
+
+def test_zero_rhs():
+    A = fi.q1(8, 1.0, 1)
+    with handle(A) as h:
+        res, x = solve(h, np.zeros(A.n), x0=np.ones(A.n))
+    assert res.status == cg_mod().CG_OK and res.iters == 0 and res.relres == 0.0
+    assert np.all(x == 0.0)
+
+
+def test_maxit_not_converged():
+    cg = cg_mod()
+    A = fi.q1(16, 1.0, 2)
+    b = oracle.spmv(A, fi.xstar(2, A.n))
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=7)
+    assert res.status == cg.CG_ENOTCONV and res.iters == 7
+    same = oracle.cg(A, b, force_iters=7)
+    assert np.linalg.norm(x - same.x) <= 1e-10 * np.linalg.norm(same.x)
+    assert abs(res.relres - same.relres_true) <= 1e-8 * same.relres_true
+
+
+def test_maxit_zero_and_exact_guess():
+    cg = cg_mod()
+    A = fi.laplace7(6)
+    xs = fi.xstar(3, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=0)
+        assert res.status == cg.CG_ENOTCONV and res.iters == 0 and np.all(x == 0)
+        res, x = solve(h, b, x0=xs, tol=1e-6)
+        assert res.status == cg.CG_OK and res.iters == 0
+
+
+def test_indefinite_breakdown():
+    cg = cg_mod()
+    A = fi.dense_to_csr(np.diag([2.0, -1.0, 3.0]))
+    with handle(A) as h:
+        res, x = solve(h, np.array([1.0, 1.0, 0.0]))
+    assert res.status == cg.CG_EBREAKDOWN
+    ref = oracle.cg(A, np.array([1.0, 1.0, 0.0]))
+    assert ref.status == oracle.BREAKDOWN and ref.iters == res.iters
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (12, 2), (20, 3)])
+def test_finite_termination_tiny(n, seed):
+    A = fi.random_spd(n, seed, density=0.5)
+    D = A.to_dense()
+    b = D @ fi.uniform(seed, 7, n)
+    with handle(A) as h:
+        res, x = solve(h, b, maxit=n + 2)
+    assert res.status == cg_mod().CG_OK and res.iters <= n + 2
+    assert np.linalg.norm(x - np.linalg.solve(D, b)) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_host_buffers_match_device_buffers_and_determinism():
+    """Host (numpy) b and x go through the same kernels: same bits; and two
+    solves give the same bits."""
+    cg = cg_mod()
+    A = fi.q1(20, 1.0, 5)
+    b = oracle.spmv(A, fi.xstar(5, A.n))
+    with handle(A) as h:
+        res_d, x_d = solve(h, b, maxit=10 * A.n)
+        res_d2, x_d2 = solve(h, b, maxit=10 * A.n)
+        xh = np.zeros(A.n)
+        res_h = cg.cg_solve(h, np.ascontiguousarray(b), xh, tol=1e-10, maxit=10 * A.n)
+    assert res_d.iters == res_d2.iters == res_h.iters
+    assert np.array_equal(x_d, x_d2) and np.array_equal(x_d, xh)
+    assert res_d.relres == res_h.relres
+
+
+def test_one_based_matrix_solve():
+    A = fi.q1(10, 1.0, 7)
+    b = oracle.spmv(A, fi.xstar(7, A.n))
+    with handle(fi.to_one_based(A)) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    check_against_oracle(A, b, res, x)
+
+
+def test_mixed_precision_q1():
+    """FP32 values/product, FP64 sums and residual replacement: reaches the FP64
+    true residual 1e-10; its solution agrees with the FP64 oracle's to the
+    accuracy the residual bound allows."""
+    cg = cg_mod()
+    A = fi.q1(24, 1.0, 3)
+    xs = fi.xstar(3, A.n)
+    b = oracle.spmv(A, xs)
+    with handle(A, precision=cg.CG_PREC_MIXED, replace_every=50) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    assert res.status == cg.CG_OK, (res, cg.last_error())
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 * 1.0000001
+    ref64 = oracle.cg(A, b, tol=1e-10, maxit=10 * A.n)
+    refmx = oracle.cg_mixed(A, b, tol=1e-10, replace_every=50)
+    assert refmx.status == oracle.OK
+    kap = kappa_estimate(A, b)
+    assert np.linalg.norm(x - ref64.x) <= 2.02 * kap * 1e-10 * np.linalg.norm(ref64.x)
+    # same algorithm as the mixed oracle: iteration counts within a few percent
+    assert abs(res.iters - refmx.iters) <= max(5, 0.05 * refmx.iters), (res.iters, refmx.iters)
+
+
+def test_wait_timeout_selftest_then_context_usable():
+    """A device-side wait that nothing will release gives up after its limit,
+    the kernel reports CG_ETIMEOUT, and the context still runs a solve."""
+    cg = cg_mod()
+    assert cg.cg_selftest_wait_timeout(200) == cg.CG_ETIMEOUT
+    A = fi.laplace7(6)
+    b = oracle.spmv(A, fi.xstar(1, A.n))
+    with handle(A) as h:
+        res, x = solve(h, b)
+    assert res.status == cg.CG_OK
