@@ -15,8 +15,8 @@ HEADER = os.path.join(ROOT, "include", "cg.h")
 
 @pytest.fixture(scope="module")
 def built():
-    from paper_2112_10823_gb300 import build
-    return build.build()
+    import __graft_entry__
+    return __graft_entry__._cuda_build_module().build()
 
 
 def declared_functions():
