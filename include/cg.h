@@ -147,6 +147,31 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
              double* relres);
 
 /*
+ * *result = sum_i x_i y_i over n elements, like cg_dot, but without a handle
+ * and without allocating anything.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate GPU memory at the moment they
+ * need a dot product, for example code running under a fixed memory budget
+ * that forbids allocation after start-up, code called from inside another
+ * allocator or memory pool that must not be re-entered, or latency-critical
+ * loops that cannot afford cudaMalloc's implicit device synchronisation.
+ * (cg_create, which cg_dot needs, allocates device memory.)
+ *
+ * x, y: device pointers to n doubles; result: device pointer to one double;
+ * stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * The scratch (per-CTA partial sums and an arrival counter) is one fixed
+ * array of about 128 KB compiled into the library, so n is limited to
+ * 33,554,432 elements (CG_EINVAL beyond, with a message).  Every GPU that
+ * loads the library holds that array until the process exits.
+ * The first call on each device looks up the array's device address (a CUDA
+ * runtime call made with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (different streams, or different host threads) race and give wrong
+ * results; serialise them.  Each call clears the counter it needs before its
+ * kernel runs.  Deterministic for a given n.
+ */
+int cg_dot_noalloc(int64_t n, const double* x, const double* y, double* result, void* stream);
+
+/*
  * Self-test of the library's bounded device-side waits (no paper
  * counterpart): launches a one-CTA kernel that waits at a grid barrier no
  * other CTA will reach.  The wait must give up after limit_ms and the kernel

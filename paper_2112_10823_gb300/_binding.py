@@ -64,6 +64,8 @@ def _load() -> ctypes.CDLL:
     lib.cg_ewmul.argtypes = [vp, i64, vp, vp, vp]
     lib.cg_solve.restype = ctypes.c_int
     lib.cg_solve.argtypes = [vp, vp, vp, dbl, i64, P(i64), P(dbl)]
+    lib.cg_dot_noalloc.restype = ctypes.c_int
+    lib.cg_dot_noalloc.argtypes = [i64, vp, vp, vp, vp]
     lib.cg_selftest_wait_timeout.restype = ctypes.c_int
     lib.cg_selftest_wait_timeout.argtypes = [i32, P(i32)]
     return lib
@@ -217,6 +219,20 @@ def cg_dot(h: Handle, x, y, out, n: int | None = None) -> None:
     _check_f64("y", y, n)
     _check_f64("out", out, 1)
     _check(lib.cg_dot(h._h, n, _ptr(x), _ptr(y), _ptr(out)), h._h)
+
+
+def cg_dot_noalloc(x, y, out, n: int | None = None, stream=None) -> None:
+    """out[0] = x . y without a handle and without any allocation (fixed
+    library scratch; n <= 33,554,432; concurrent calls race)."""
+    import torch
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    _check_f64("out", out, 1)
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(lib.cg_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(out), s))
 
 
 def cg_axpy(h: Handle, a: float, x, y, n: int | None = None) -> None:

@@ -149,3 +149,67 @@ cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStre
 }
 
 }  // namespace cgk
+
+// ---------------------------------------------------------------------------
+// Dot product without any allocation (cg_dot_noalloc).
+//
+// Same kernel as cg_dot, launched with one CTA per kNoAllocElemsPerCta
+// elements, with its scratch in a fixed device array compiled into the
+// library instead of memory the caller or a handle allocates.  The array holds
+// kNoAllocMaxCtas per-CTA partial sums followed by the arrival counter, so the
+// largest accepted length is kNoAllocMaxCtas * kNoAllocElemsPerCta elements.
+// Every GPU that loads the library keeps this array (about 128 KB) until the
+// process exits.
+#include <mutex>
+
+namespace cgk {
+
+constexpr int kNoAllocMaxCtas = 16384;
+constexpr int64_t kNoAllocElemsPerCta = static_cast<int64_t>(kBlock) * 8;
+constexpr int64_t kNoAllocMaxN = static_cast<int64_t>(kNoAllocMaxCtas) * kNoAllocElemsPerCta;
+
+// [0, kNoAllocMaxCtas): partial sums; the next slot holds the arrival counter.
+static __device__ __align__(256) double g_dot_noalloc_scratch[kNoAllocMaxCtas + 32];
+
+int64_t dot_noalloc_max_n() { return kNoAllocMaxN; }
+
+// Device address of the scratch on the current device.  In host code the
+// array's name is only a stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device (with that device current), and is
+// cached.  The first call on a device therefore makes a runtime call that must
+// not happen inside a stream capture.
+static cudaError_t noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* cache[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_dot_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    cache[dev] = p;
+  }
+  *out = cache[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_dot_noalloc(int64_t n, const double* x, const double* y, double* out, cudaStream_t s) {
+  if (n < 0 || n > kNoAllocMaxN) return cudaErrorInvalidValue;
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return e;
+  unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocMaxCtas);
+  // The counter must start at zero; the kernel's last CTA also resets it, but a
+  // call that never finished would leave it set.
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (n + kNoAllocElemsPerCta - 1) / kNoAllocElemsPerCta;
+  if (grid < 1) grid = 1;
+  dot_kernel<<<static_cast<unsigned int>(grid), kBlock, 0, s>>>(n, x, y, out, scratch, counter);
+  return cudaGetLastError();
+}
+
+}  // namespace cgk

@@ -12,6 +12,8 @@
 
 namespace cgk {
 cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
+cudaError_t launch_dot_noalloc(int64_t n, const double* x, const double* y, double* out, cudaStream_t s);
+int64_t dot_noalloc_max_n();
 }
 
 struct cg_ctx {
@@ -463,6 +465,17 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   if (st == CG_EBREAKDOWN) return fail(h, CG_EBREAKDOWN, "cg_solve: breakdown (p.Ap <= 0 or not finite)");
   if (st == CG_ENOTCONV) return fail(h, CG_ENOTCONV, "cg_solve: maxit reached before the tolerance");
   return st;
+}
+
+int cg_dot_noalloc(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  const int64_t max_n = cgk::dot_noalloc_max_n();
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(nullptr, CG_EINVAL, "cg_dot_noalloc: bad arguments");
+  if (n > max_n)
+    return fail(nullptr, CG_EINVAL,
+                "cg_dot_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch capacity of " +
+                    std::to_string(max_n) + " elements; use cg_dot");
+  cudaError_t e = cgk::launch_dot_noalloc(n, x, y, result, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CG_OK : cuda_fail(nullptr, e, "cg_dot_noalloc");
 }
 
 int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status) {
