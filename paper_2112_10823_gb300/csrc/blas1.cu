@@ -165,7 +165,7 @@ cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStre
 namespace cgk {
 
 constexpr int kNoAllocMaxCtas = 16384;
-constexpr int64_t kNoAllocElemsPerCta = static_cast<int64_t>(kBlock) * 8;
+constexpr int64_t kNoAllocElemsPerCta = 2048;
 constexpr int64_t kNoAllocMaxN = static_cast<int64_t>(kNoAllocMaxCtas) * kNoAllocElemsPerCta;
 
 // [0, kNoAllocMaxCtas): partial sums; the next slot holds the arrival counter.

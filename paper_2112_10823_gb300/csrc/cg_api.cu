@@ -99,9 +99,17 @@ bool is_device_ptr(const void* p) {
 
 // Row partition of the persistent kernels.  Rows are split into `nblocks`
 // contiguous ranges of about equal cost (stored entries + kRowCost per row,
-// the per-row vector work), and each range into chunks of at most kChunkRows
-// rows and kChunkNnz entries.  A row longer than kChunkNnz is a chunk alone.
+// the per-row vector work), and each range into compute chunks of at most
+// kChunkNnz entries.  A chunk whose rows all hold <= 16 entries is computed
+// one thread per row (<= kBlock rows); rows of <= 64 entries two threads per
+// row (<= kBlock/2 rows); longer rows one warp per row.  A row longer than
+// kChunkNnz is a chunk alone, streamed from global memory.
 constexpr int64_t kRowCost = 6;
+
+int chunk_mode_for(int64_t maxlen) {
+  return maxlen <= 16 ? cgk::kThreadPerRow : (maxlen <= 64 ? cgk::kPairPerRow : cgk::kWarpPerRow);
+}
+int64_t chunk_row_cap(int mode) { return mode == cgk::kPairPerRow ? cgk::kBlock / 2 : cgk::kBlock; }
 
 void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, std::vector<int32_t>& chunk_row,
                      std::vector<int32_t>& chunk_mode, std::vector<int32_t>& block_chunk) {
@@ -131,17 +139,17 @@ void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, std
       }
       const int64_t start = row;
       int64_t cnt = 0, maxlen = 0;
-      while (row < end && row - start < cgk::kChunkRows) {
+      while (row < end) {
         const int64_t len = rp[row + 1] - rp[row];
         if (len > cgk::kChunkNnz || cnt + len > cgk::kChunkNnz) break;
+        const int64_t newmax = len > maxlen ? len : maxlen;
+        if (row - start + 1 > chunk_row_cap(chunk_mode_for(newmax))) break;
         cnt += len;
-        if (len > maxlen) maxlen = len;
+        maxlen = newmax;
         ++row;
       }
-      const int64_t rows = row - start;
-      const bool warp = (cnt > 48 * rows) || maxlen > 256;
       chunk_row.push_back(static_cast<int32_t>(start));
-      chunk_mode.push_back(warp ? cgk::kWarpPerRow : cgk::kThreadPerRow);
+      chunk_mode.push_back(chunk_mode_for(maxlen));
     }
   }
   block_chunk[nblocks] = static_cast<int32_t>(chunk_row.size());

@@ -1,6 +1,6 @@
 // Device-side building blocks of the CG kernels: PTX wrappers for 1-D TMA
 // bulk copies and mbarriers, deterministic reductions, the bounded grid
-// barrier of the persistent solve, and the shared-memory-staged CSR product.
+// barrier of the persistent solve, and the CSR product fed by a TMA ring.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -90,70 +90,115 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// Sum of `v` over the CTA, in a fixed order; every thread gets the same value.
-// The per-thread values go through shared memory and only warp 0 adds them
-// (8 sequential adds per lane, then a butterfly), which keeps the number of
-// FP64 warp instructions small: FP64 issue is scarce on this GPU.
-// `red` holds at least kBlock + 1 doubles.  Must be called by all threads.
+// Sum of `v` over the CTA in a fixed order (FP64 adds); every thread gets the
+// same value.  `red` holds blockDim.x + 1 doubles (blockDim.x a multiple of
+// 32, at most 1024).  All threads must call it.
 __device__ __forceinline__ double block_sum(double v, double* red) {
-  __syncthreads();  // earlier users of `red` are done
+  const int nt = blockDim.x;
+  __syncthreads();
   red[threadIdx.x] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
     double s = red[threadIdx.x];
-#pragma unroll
-    for (int j = 1; j < kWarps; ++j) s += red[threadIdx.x + 32 * j];
+    for (int j = 32 + threadIdx.x; j < nt; j += 32) s += red[j];
     s = warp_sum(s);
-    if (threadIdx.x == 0) red[kBlock] = s;
+    if (threadIdx.x == 0) red[nt] = s;
   }
   __syncthreads();
-  return red[kBlock];
+  return red[nt];
 }
 
-// Two sums at once (same order rules as block_sum).  `red` holds 2*kBlock+2.
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
-  __syncthreads();
-  red[threadIdx.x] = a;
-  red[kBlock + threadIdx.x] = b;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = red[threadIdx.x], t = red[kBlock + threadIdx.x];
-#pragma unroll
-    for (int j = 1; j < kWarps; ++j) {
-      s += red[threadIdx.x + 32 * j];
-      t += red[kBlock + threadIdx.x + 32 * j];
-    }
-    s = warp_sum(s);
-    t = warp_sum(t);
-    if (threadIdx.x == 0) {
-      red[2 * kBlock] = s;
-      red[2 * kBlock + 1] = t;
-    }
+// Scratch of the fixed-point CTA sum (shared memory).
+struct FxScratch {
+  long long m[kWarps];
+  int32_t e[kWarps];
+  int32_t nf[kWarps];
+  double result;
+};
+
+// Sum over the CTA of one double per thread, exactly in fixed point.
+//
+// FP64 adds cost 64 cycles of latency each on this GPU, so a tree of them over
+// 512 values sits on the critical path of every CG step.  Instead each value is
+// rounded to a common fixed-point grid set by the largest exponent E in the
+// CTA (spacing 2^(E-1074), i.e. about 2^-51 of the largest value, leaving 10
+// bits of headroom for up to 1024 terms), the integers are added exactly with
+// integer adds (order-independent, so the sum is deterministic whatever the
+// order of arrival), and the total is rounded once back to FP64.  Zero and
+// subnormal values count as zero; an infinite or NaN value makes the sum NaN.
+// Thread 0 converts the total; every thread receives it through shared memory.
+// Requires blockDim.x == kBlock.
+__device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((bits >> 52) & 0x7ffull);
+  const unsigned int ew = __reduce_max_sync(0xffffffffu, static_cast<unsigned int>(e));
+  const int nfw = __any_sync(0xffffffffu, e == 0x7ff);
+  __syncthreads();  // earlier users of sc are done
+  if (lane == 0) {
+    sc->e[warp] = static_cast<int32_t>(ew);
+    sc->nf[warp] = nfw;
   }
   __syncthreads();
-  a = red[2 * kBlock];
-  b = red[2 * kBlock + 1];
+  int E = 0, nf = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    E = max(E, static_cast<int>(sc->e[w]));
+    nf |= sc->nf[w];
+  }
+  long long m = 0;
+  if (e != 0 && !nf) {
+    const int s = E - e + 1;  // >= 1
+    if (s < 64) {
+      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const unsigned long long rnd = (M + (1ull << (s - 1))) >> s;
+      m = (bits >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if (lane == 0) sc->m[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += sc->m[w];
+    double r;
+    if (nf) r = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+    else if (E == 0) r = 0.0;
+    else r = ldexp(static_cast<double>(tot), E - 1074);
+    sc->result = r;
+  }
+  __syncthreads();
+  return sc->result;
 }
 
 // ------------------------------------------------------------ grid barrier
 
-// Bounded grid-wide barrier for a cooperative (co-resident) launch.  Thread 0
-// of each CTA adds one arrival to a monotonic 64-bit counter with release
-// semantics and spins with acquire loads until all CTAs of this round have
-// arrived; the fence afterwards makes every write that preceded any CTA's
-// arrival visible to all threads of this CTA.  A wait longer than
-// `limit_ns`, or an abort raised by another CTA, makes it return false in
-// every thread of the CTA (the caller then leaves the kernel).
+// Bounded grid-wide barrier for a cooperative (co-resident) launch, split in
+// an arrive and a wait half so that a CTA can do independent work between
+// them.  Thread 0 of each CTA adds one arrival to a monotonic 64-bit counter
+// with release semantics and later spins with acquire loads until all CTAs of
+// this round have arrived; the fence afterwards makes every write that
+// preceded any CTA's arrival visible to all threads of this CTA.  A wait
+// longer than `limit_ns`, or an abort raised by another CTA, makes wait()
+// return false in every thread of the CTA (the caller then leaves the kernel).
 struct GridBarrier {
   unsigned long long target = 0;
 
-  __device__ __forceinline__ bool sync(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
-                                       int32_t* flag_smem) {
+  // All threads call; the CTA's writes before this point are published.
+  __device__ __forceinline__ void arrive(SolveCtrl* ctrl) {
     __syncthreads();
+    target += gridDim.x;
     if (threadIdx.x == 0) {
-      target += gridDim.x;
       __threadfence();
       red_release_add_u64(&ctrl->barrier, 1ull);
+    }
+  }
+
+  __device__ __forceinline__ bool wait(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
+                                       int32_t* flag_smem) {
+    if (threadIdx.x == 0) {
       int32_t ok = 1;
       unsigned long long t0 = 0;
       uint32_t spins = 0;
@@ -176,133 +221,252 @@ struct GridBarrier {
     __syncthreads();
     return *flag_smem != 0;
   }
+
+  __device__ __forceinline__ bool sync(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
+                                       int32_t* flag_smem) {
+    arrive(ctrl);
+    return wait(ctrl, limit_ns, site, flag_smem);
+  }
 };
 
-// ------------------------------------------------------- staged CSR product
+// ------------------------------------------------------ streamed CSR product
 
-// Shared memory of the staged product: kStages stages of values + column
-// indices, their mbarriers, a reduction scratch and a broadcast flag, laid out
-// by offsets in one dynamic shared-memory buffer.  The value area of a stage
-// is sized for FP64; the FP32 product of the mixed-precision solve uses the
-// first half of it, so both products share the same stages and mbarriers.
-struct SpmvSmem {
-  static constexpr size_t kValBytes = (sizeof(double) * kStageVal + 15) & ~size_t(15);
-  static constexpr size_t kColBytes = (sizeof(int32_t) * kStageCol + 15) & ~size_t(15);
-  static constexpr size_t kStageBytes = kValBytes + kColBytes;
-  static constexpr size_t kRedBytes = sizeof(double) * (2 * kBlock + 4);
-  static constexpr size_t kBytes = kStages * kStageBytes + kRedBytes + 8 * kStages + 16;
+// Shared memory of the streamed product: the value ring (sized for FP64; the
+// FP32 product uses its first half), the column-index ring, one mbarrier per
+// ring slot, reduction scratch and a few broadcast words.
+struct RingSmem {
+  static constexpr size_t kValBytes = sizeof(double) * kRing;
+  static constexpr size_t kColBytes = sizeof(int32_t) * kRing;
+  static constexpr size_t kBarOff = kValBytes + kColBytes;
+  static constexpr size_t kRedOff = kBarOff + 8 * kSlots;
+  static constexpr size_t kRedBytes = sizeof(double) * (kBlock + 8);
+  static constexpr size_t kFxOff = kRedOff + kRedBytes;
+  static constexpr size_t kFxBytes = (sizeof(FxScratch) + 15) & ~size_t(15);
+  static constexpr size_t kMiscOff = kFxOff + kFxBytes;
+  static constexpr size_t kBytes = kMiscOff + 64;
 
   unsigned char* base;
   template <typename T>
-  __device__ T* val(int s) const { return reinterpret_cast<T*>(base + s * kStageBytes); }
-  __device__ int32_t* col(int s) const {
-    return reinterpret_cast<int32_t*>(base + s * kStageBytes + kValBytes);
-  }
-  __device__ double* red() const { return reinterpret_cast<double*>(base + kStages * kStageBytes); }
-  __device__ uint64_t* bar(int s) const {
-    return reinterpret_cast<uint64_t*>(base + kStages * kStageBytes + kRedBytes) + s;
-  }
-  __device__ int32_t* flag() const {
-    return reinterpret_cast<int32_t*>(base + kStages * kStageBytes + kRedBytes + 8 * kStages);
-  }
+  __device__ T* val() const { return reinterpret_cast<T*>(base); }
+  __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + kValBytes); }
+  __device__ uint64_t* bar(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + s; }
+  __device__ double* red() const { return reinterpret_cast<double*>(base + kRedOff); }
+  __device__ FxScratch* fx() const { return reinterpret_cast<FxScratch*>(base + kFxOff); }
+  __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + kMiscOff); }
+  __device__ double* scalars() const { return reinterpret_cast<double*>(base + kMiscOff + 16); }
 };
 
-// Per-CTA pipeline state of the staged product; lives in registers and is
-// uniform across the CTA.
-struct StagePipe {
-  uint32_t phase = 0;     // bit s: parity the next completion of stage s will have
-  uint32_t issued = 0;    // staged chunks issued so far
-  uint32_t consumed = 0;  // staged chunks consumed so far
+// Per-CTA state of the matrix stream; in registers, uniform across the CTA.
+// Pieces are numbered globally (across passes) so that the slot of a piece is
+// (global number % kSlots) and its mbarrier phase (global number / kSlots) & 1.
+struct RingState {
+  int kb = 0;            // first entry of the CTA's range, rounded down to a multiple of 4
+  int ke = 0;            // end of the CTA's entry range
+  int npieces = 0;       // pieces per pass
+  uint32_t gbase = 0;    // global number of piece 0 of the current pass
+  int issued = 0;        // pieces of the current pass issued
+  int waited = 0;        // pieces of the current pass seen complete
+  int released = 0;      // pieces of the current pass whose slots may be refilled
+  int pre_type = 0;      // value size (4 or 8) of pieces prefetched for the next pass, 0 = none
+  int pre_count = 0;     // pieces of the next pass already issued
 };
 
-__device__ __forceinline__ void stage_init(const SpmvSmem& sm) {
+__device__ __forceinline__ void ring_init(const RingSmem& sm, RingState& rs, const DevCsr& A, int row0,
+                                          int row1) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(sm.bar(s), 1);
+    for (int s = 0; s < kSlots; ++s) mbar_init(sm.bar(s), 1);
     fence_mbar_init();
   }
   __syncthreads();
+  rs.kb = A.row_ptr[row0] & ~3;
+  rs.ke = A.row_ptr[row1];
+  // a CTA without rows streams nothing (kb may sit below ke after rounding)
+  rs.npieces = row1 > row0 ? (rs.ke - rs.kb + kPiece - 1) >> kPieceLog : 0;
 }
 
-// Issue the bulk copies of chunk c (values of type T, column indices) into
-// stage `s`.  Called by one thread.
+// Ring position of the first entry of piece 0 of the pass starting at gbase.
+__device__ __forceinline__ int ring_pos_of_piece0(uint32_t gbase) {
+  return static_cast<int>((gbase % kSlots) * kPiece);
+}
+
+// Issue piece j of the pass starting at gbase (values of type T).  One thread.
 template <typename T>
-__device__ __forceinline__ void stage_issue(const SpmvSmem& sm, int s, const int32_t* row_ptr,
-                                            const int32_t* col_idx, const T* val, int r0, int r1) {
-  constexpr int kAlignV = 16 / sizeof(T);
-  const int k0 = row_ptr[r0], k1 = row_ptr[r1];
-  const int kv0 = k0 & ~(kAlignV - 1);
-  const int kc0 = k0 & ~3;
-  const uint32_t bv = (static_cast<uint32_t>(k1 - kv0) * sizeof(T) + 15u) & ~15u;
-  const uint32_t bc = (static_cast<uint32_t>(k1 - kc0) * 4u + 15u) & ~15u;
+__device__ __forceinline__ void ring_issue(const RingSmem& sm, const RingState& rs, uint32_t gbase, int j,
+                                           const T* val, const int32_t* col) {
+  const int e0 = rs.kb + j * kPiece;
+  int e1 = e0 + kPiece;
+  const int ke4 = (rs.ke + 3) & ~3;  // copy whole 16-byte groups (<= 3 padding entries)
+  if (e1 > ke4) e1 = ke4;
+  const int slot = static_cast<int>((gbase + static_cast<uint32_t>(j)) % kSlots);
+  const int pos = slot * kPiece;
+  const uint32_t bv = static_cast<uint32_t>(e1 - e0) * sizeof(T);
+  const uint32_t bc = static_cast<uint32_t>(e1 - e0) * 4u;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(sm.bar(s), bv + bc);
-  if (bv) bulk_g2s(sm.val<T>(s), val + kv0, bv, sm.bar(s));
-  if (bc) bulk_g2s(sm.col(s), col_idx + kc0, bc, sm.bar(s));
+  mbar_arrive_expect_tx(sm.bar(slot), bv + bc);
+  bulk_g2s(sm.val<T>() + pos, val + e0, bv, sm.bar(slot));
+  bulk_g2s(sm.col() + pos, col + e0, bc, sm.bar(slot));
 }
 
-// Wait (bounded) for stage s.  The outcome is made uniform over the CTA:
-// false in every thread if any thread gave up.
-__device__ __forceinline__ bool stage_wait(const SpmvSmem& sm, int s, uint32_t parity,
-                                           unsigned long long limit_ns) {
+// Wait (bounded) for global piece g; returns false if the wait gave up.
+__device__ __forceinline__ bool ring_wait_global(const RingSmem& sm, uint32_t g, unsigned long long limit_ns) {
+  const int slot = static_cast<int>(g % kSlots);
+  const uint32_t parity = (g / kSlots) & 1u;
   uint32_t spins = 0;
   unsigned long long t0 = 0;
-  int ok = 1;
-  while (!mbar_try_wait(sm.bar(s), parity)) {
+  while (!mbar_try_wait(sm.bar(slot), parity)) {
     if ((++spins & 63u) == 0) {
-      unsigned long long now = global_timer_ns();
+      const unsigned long long now = global_timer_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > limit_ns) { ok = 0; break; }
+      else if (now - t0 > limit_ns) return false;
     }
   }
+  return true;
+}
+
+// Wait for pieces [rs.waited, upto) of the current pass, in order.  Called by
+// all threads; the outcome is made uniform over the CTA.
+__device__ __forceinline__ bool ring_wait_upto(const RingSmem& sm, RingState& rs, int upto,
+                                               unsigned long long limit_ns) {
+  int ok = 1;
+  for (int j = rs.waited; j < upto; ++j)
+    if (!ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns)) ok = 0;
+  if (upto > rs.waited) rs.waited = upto;
   return __syncthreads_and(ok) != 0;
 }
 
-// Gather-multiply-accumulate of one row held in shared memory: with
-// jv = k - kv0 and jc = k - kc0 the stage positions of entry k,
-//   s = sum_{k in [ks, ke)} sv[jv] * x[sc[jc]], in order, with FMA.
-// Gathers are issued 8 at a time to keep several loads in flight.
-template <typename T, typename X, typename Acc>
-__device__ __forceinline__ Acc row_dot_smem(const T* sv, const int32_t* sc, int jv, int jc, int len,
-                                            const X* x) {
+// Keep the ring full: issue pieces while slots are free.  Thread 0 issues;
+// the counters advance in every thread.
+template <typename T>
+__device__ __forceinline__ void ring_fill(const RingSmem& sm, RingState& rs, const T* val, const int32_t* col) {
+  int lim = rs.released + kSlots;
+  if (lim > rs.npieces) lim = rs.npieces;
+  if (threadIdx.x == 0)
+    for (int j = rs.issued; j < lim; ++j) ring_issue<T>(sm, rs, rs.gbase, j, val, col);
+  if (lim > rs.issued) rs.issued = lim;
+}
+
+// Start a pass over values of type T: adopt the pieces prefetched for it, or
+// first wait out prefetched pieces of the other type and skip past them.
+template <typename T>
+__device__ __forceinline__ bool ring_begin_pass(const RingSmem& sm, RingState& rs, const T* val,
+                                                const int32_t* col, unsigned long long limit_ns) {
+  if (rs.pre_count > 0 && rs.pre_type != static_cast<int>(sizeof(T))) {
+    int ok = 1;
+    for (int j = 0; j < rs.pre_count; ++j)
+      if (!ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns)) ok = 0;
+    if (!__syncthreads_and(ok)) return false;
+    rs.gbase += static_cast<uint32_t>(rs.pre_count);
+    rs.pre_count = 0;
+  }
+  rs.issued = rs.pre_count;
+  rs.waited = 0;
+  rs.released = 0;
+  rs.pre_count = 0;
+  rs.pre_type = 0;
+  __syncthreads();  // no thread still reads the ring from an earlier pass
+  ring_fill<T>(sm, rs, val, col);
+  return true;
+}
+
+// End a pass: every piece of it has been consumed.  Optionally issue the
+// first pieces of the next pass (values of type Tn) so that they load during
+// whatever the CTA does before that pass.
+template <typename Tn>
+__device__ __forceinline__ void ring_end_pass(const RingSmem& sm, RingState& rs, const Tn* next_val,
+                                              const int32_t* col) {
+  rs.gbase += static_cast<uint32_t>(rs.npieces);
+  rs.issued = rs.waited = rs.released = 0;
+  rs.pre_count = 0;
+  rs.pre_type = 0;
+  if (next_val != nullptr && rs.npieces > 0) {
+    const int cnt = rs.npieces < kSlots ? rs.npieces : kSlots;
+    __syncthreads();  // every thread is done reading the ring
+    if (threadIdx.x == 0)
+      for (int j = 0; j < cnt; ++j) ring_issue<Tn>(sm, rs, rs.gbase, j, next_val, col);
+    rs.pre_count = cnt;
+    rs.pre_type = static_cast<int>(sizeof(Tn));
+  }
+}
+
+// Before leaving the kernel on an error path: wait (bounded) for the copies
+// this CTA still has in flight, so no bulk copy lands after the CTA is gone.
+__device__ __forceinline__ void ring_drain(const RingSmem& sm, RingState& rs, unsigned long long limit_ns) {
+  for (int j = rs.waited; j < rs.issued; ++j) ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns);
+  for (int j = 0; j < rs.pre_count; ++j) ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns);
+}
+
+// Dot product of one row segment held in the ring: entries at ring positions
+// pos, pos+1, ... (masked), len of them, in storage order, with FMA.  Up to U
+// entries take a fully unrolled path that issues every gather before the
+// first multiply-add; longer segments go 8 at a time.
+template <typename T, typename X, typename Acc, int U>
+__device__ __forceinline__ Acc seg_dot(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
   Acc s = Acc(0);
+  if (len <= U) {
+    // all gathers first (only they have long latency), then the FMAs with
+    // the values read from shared memory as they are consumed
+    X xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
+    return s;
+  }
   int t = 0;
   for (; t + 8 <= len; t += 8) {
-    int c[8];
     X xv[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = sc[jc + t + u];
+    for (int u = 0; u < 8; ++u) xv[u] = x[rc[(pos + t + u) & kRingMask]];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = x[c[u]];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s = fma(Acc(sv[jv + t + u]), Acc(xv[u]), s);
+    for (int u = 0; u < 8; ++u) s = fma(Acc(rv[(pos + t + u) & kRingMask]), Acc(xv[u]), s);
   }
-  for (; t < len; ++t) s = fma(Acc(sv[jv + t]), Acc(x[sc[jc + t]]), s);
+  for (; t < len; ++t) {
+    const int p = (pos + t) & kRingMask;
+    s = fma(Acc(rv[p]), Acc(x[rc[p]]), s);
+  }
   return s;
 }
 
-// y rows of chunk [r0, r1) from stage s (thread- or warp-per-row), each result
-// handed to epi(i, yi) by the thread that computed it.
+// Rows of chunk [r0, r1) from the ring; each result goes to epi(i, yi) from
+// the thread that holds it.  Entry k sits at ring position (k - kb + off) &
+// kRingMask.
 template <typename T, typename X, typename Acc, typename Epi>
-__device__ __forceinline__ void chunk_compute_staged(const SpmvSmem& sm, int s, int mode,
-                                                     const int32_t* row_ptr, int r0, int r1, const X* x,
-                                                     Epi& epi) {
-  constexpr int kAlignV = 16 / sizeof(T);
-  const int k0 = row_ptr[r0];
-  const int kv0 = k0 & ~(kAlignV - 1), kc0 = k0 & ~3;
-  const T* sv = sm.val<T>(s);
-  const int32_t* sc = sm.col(s);
+__device__ __forceinline__ void chunk_compute_ring(const RingSmem& sm, int mode, const int32_t* row_ptr, int r0,
+                                                   int r1, int kb, int off, const X* x, Epi& epi) {
+  const T* rv = sm.val<T>();
+  const int32_t* rc = sm.col();
   if (mode == kThreadPerRow) {
     const int i = r0 + static_cast<int>(threadIdx.x);
     if (i < r1) {
       const int ks = row_ptr[i], ke = row_ptr[i + 1];
-      epi(i, row_dot_smem<T, X, Acc>(sv, sc, ks - kv0, ks - kc0, ke - ks, x));
+      epi(i, seg_dot<T, X, Acc, 16>(rv, rc, ks - kb + off, ke - ks, x));
     }
+  } else if (mode == kPairPerRow) {
+    const int i = r0 + static_cast<int>(threadIdx.x >> 1);
+    const int h = threadIdx.x & 1;
+    Acc part = Acc(0);
+    if (i < r1) {
+      const int ks = row_ptr[i], ke = row_ptr[i + 1];
+      const int half = (ke - ks + 1) >> 1;
+      const int a = h ? ks + half : ks;
+      const int len = h ? (ke - ks - half) : half;
+      part = seg_dot<T, X, Acc, 16>(rv, rc, a - kb + off, len, x);
+    }
+    // first half + second half: the same value in both lanes (commutative add)
+    const Acc other = __shfl_xor_sync(0xffffffffu, part, 1);
+    const Acc s = part + other;
+    if (h == 0 && i < r1) epi(i, s);
   } else {  // kWarpPerRow
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = r0 + w; i < r1; i += kWarps) {
       const int ks = row_ptr[i], ke = row_ptr[i + 1];
       Acc acc = Acc(0);
-      for (int k = ks + lane; k < ke; k += 32) acc = fma(Acc(sv[k - kv0]), Acc(x[sc[k - kc0]]), acc);
+      for (int k = ks + lane; k < ke; k += 32) {
+        const int p = (k - kb + off) & kRingMask;
+        acc = fma(Acc(rv[p]), Acc(x[rc[p]]), acc);
+      }
       if constexpr (sizeof(Acc) == 8) acc = warp_sum(acc);
       else acc = warp_sum_f(acc);
       if (lane == 0) epi(i, acc);
@@ -310,7 +474,7 @@ __device__ __forceinline__ void chunk_compute_staged(const SpmvSmem& sm, int s, 
   }
 }
 
-// One row longer than a stage, streamed from global memory by the whole CTA.
+// One row longer than kChunkNnz, streamed from global memory by the whole CTA.
 template <typename T, typename X, typename Acc, typename Epi>
 __device__ __forceinline__ void chunk_compute_long(const int32_t* row_ptr, const int32_t* col_idx,
                                                    const T* val, int i, const X* x, double* red, Epi& epi) {
@@ -322,58 +486,45 @@ __device__ __forceinline__ void chunk_compute_long(const int32_t* row_ptr, const
   if (threadIdx.x == 0) epi(i, static_cast<Acc>(tot));
 }
 
-// The product over chunks [c0, c1) of A (values `val` of type T), staged
-// through shared memory with one chunk in flight ahead of the one being
-// computed.  Returns false if a wait gave up (the caller leaves the kernel).
-template <typename T, typename X, typename Acc, typename Epi>
-__device__ __forceinline__ bool spmv_pass(const SpmvSmem& sm, StagePipe& pp, const DevCsr& A, const T* val,
-                                          int c0, int c1, const X* x, Epi& epi, unsigned long long limit_ns) {
+// The product over the CTA's chunks [c0, c1) with values `val` of type T,
+// gathering x.  The pass starts from the pieces prefetched for it (if any)
+// and ends by prefetching the first pieces of the next pass (next_val, of
+// type Tn; nullptr for none).  Returns false if a wait gave up.
+template <typename T, typename X, typename Acc, typename Tn, typename Epi>
+__device__ __forceinline__ bool spmv_pass(const RingSmem& sm, RingState& rs, const DevCsr& A, const T* val,
+                                          int c0, int c1, const X* x, Epi& epi, const Tn* next_val,
+                                          unsigned long long limit_ns) {
   const int32_t* row_ptr = A.row_ptr;
   const int32_t* cr = A.chunk_row;
   const int32_t* cm = A.chunk_mode;
-  // next staged chunk at or after c
-  auto next_staged = [&](int c) {
-    while (c < c1 && cm[c] == kBlockPerRow) ++c;
-    return c;
-  };
-  int nxt = next_staged(c0);
-  if (nxt < c1 && threadIdx.x == 0)
-    stage_issue<T>(sm, static_cast<int>(pp.issued & 1u), row_ptr, A.col_idx, val, cr[nxt], cr[nxt + 1]);
-  if (nxt < c1) pp.issued++;
+  if (!ring_begin_pass<T>(sm, rs, val, A.col_idx, limit_ns)) return false;
+  const int off = ring_pos_of_piece0(rs.gbase);
   for (int c = c0; c < c1; ++c) {
     const int mode = cm[c];
+    const int r0 = cr[c], r1 = cr[c + 1];
+    const int k1 = row_ptr[r1];
     if (mode == kBlockPerRow) {
-      chunk_compute_long<T, X, Acc>(row_ptr, A.col_idx, val, cr[c], x, sm.red(), epi);
-      continue;
+      chunk_compute_long<T, X, Acc>(row_ptr, A.col_idx, val, r0, x, sm.red(), epi);
+    } else {
+      const int k0 = row_ptr[r0];
+      if (k1 > k0 && !ring_wait_upto(sm, rs, ((k1 - 1 - rs.kb) >> kPieceLog) + 1, limit_ns)) return false;
+      chunk_compute_ring<T, X, Acc>(sm, mode, row_ptr, r0, r1, rs.kb, off, x, epi);
     }
-    // c is the staged chunk number pp.consumed; put the next one in flight.
-    nxt = next_staged(c + 1);
-    if (nxt < c1) {
-      if (threadIdx.x == 0)
-        stage_issue<T>(sm, static_cast<int>(pp.issued & 1u), row_ptr, A.col_idx, val, cr[nxt], cr[nxt + 1]);
-      pp.issued++;
+    __syncthreads();  // the chunk's ring entries are consumed
+    // Release the pieces that end before the next chunk's first entry.  A slot
+    // is refilled only after its piece is complete, so pieces are waited for
+    // before release; a row longer than the ring (streamed from global memory)
+    // advances the ring in steps of at most kSlots pieces.
+    const int rel = (c + 1 == c1) ? rs.npieces : ((k1 - rs.kb) >> kPieceLog);
+    while (rel > rs.released) {
+      const int upto = rel < rs.issued ? rel : rs.issued;
+      if (!ring_wait_upto(sm, rs, upto, limit_ns)) return false;
+      rs.released = upto;
+      ring_fill<T>(sm, rs, val, A.col_idx);
     }
-    const int s = static_cast<int>(pp.consumed & 1u);
-    const uint32_t parity = (pp.phase >> s) & 1u;
-    if (!stage_wait(sm, s, parity, limit_ns)) return false;
-    pp.phase ^= (1u << s);
-    chunk_compute_staged<T, X, Acc>(sm, s, mode, row_ptr, cr[c], cr[c + 1], x, epi);
-    __syncthreads();  // stage s is free again before it is refilled
-    pp.consumed++;
   }
+  ring_end_pass<Tn>(sm, rs, next_val, A.col_idx);
   return true;
-}
-
-// Before leaving the kernel on an error path: wait (bounded) for every copy
-// this CTA still has in flight, so no bulk copy lands in shared memory after
-// the CTA is gone.
-__device__ __forceinline__ void stage_drain(const SpmvSmem& sm, StagePipe& pp, unsigned long long limit_ns) {
-  while (pp.consumed < pp.issued) {
-    const int s = static_cast<int>(pp.consumed & 1u);
-    stage_wait(sm, s, (pp.phase >> s) & 1u, limit_ns);
-    pp.phase ^= (1u << s);
-    pp.consumed++;
-  }
 }
 
 }  // namespace cgk

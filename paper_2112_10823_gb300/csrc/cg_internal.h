@@ -6,30 +6,33 @@
 
 namespace cgk {
 
-// Every kernel runs 256-thread CTAs.
-constexpr int kBlock = 256;
+// The persistent kernels run one 512-thread CTA per SM.
+constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / 32;
-// A SpMV chunk is a run of consecutive rows computed together by one CTA:
-// at most kChunkRows rows and at most kChunkNnz stored entries, so that its
-// values and column indices fit one shared-memory stage.  A single row
-// longer than kChunkNnz forms a chunk of its own and is streamed from global
-// memory by the whole CTA.
-constexpr int kChunkRows = 256;
-constexpr int kChunkNnz = 8192;
-// Shared-memory stage: values (8 B) and column indices (4 B) of one chunk plus
-// alignment slack (a bulk copy starts on a 16-byte boundary, so up to 1 value
-// or 3 indices in front of the chunk are copied as well).
-constexpr int kStageVal = kChunkNnz + 2;
-constexpr int kStageCol = kChunkNnz + 4;
-constexpr int kStages = 2;
+
+// Matrix stream of a CTA: its CSR values and column indices flow through a
+// shared-memory ring of kSlots pieces of kPiece entries, each piece one pair
+// of 1-D TMA bulk copies completing on the slot's mbarrier.
+constexpr int kPieceLog = 11;
+constexpr int kPiece = 1 << kPieceLog;  // 2048 entries
+constexpr int kSlots = 8;
+constexpr int kRing = kPiece * kSlots;  // 16384 entries: 128 KB of FP64 values + 64 KB of indices
+constexpr int kRingMask = kRing - 1;
+// A compute chunk is a run of consecutive rows computed together: at most
+// kChunkNnz entries (half the ring, so the next pieces stream in meanwhile)
+// and at most kBlock rows (one thread per row) or kBlock/2 rows (two threads
+// per row).  A row longer than kChunkNnz is a chunk of its own, streamed from
+// global memory by the whole CTA.
+constexpr int kChunkNnz = kRing / 2;
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
 constexpr int kPadEntries = 8;
 
 enum ChunkMode : int32_t {
-  kThreadPerRow = 0,  // short rows: thread t computes row r0 + t from shared memory
-  kWarpPerRow = 1,    // longer rows: warp w computes rows r0 + w, r0 + w + 8, ... from shared memory
-  kBlockPerRow = 2,   // one row longer than a stage: streamed from global memory by the CTA
+  kThreadPerRow = 0,  // rows of <= 16 entries: thread t computes row r0 + t
+  kPairPerRow = 1,    // rows of <= 64 entries: threads 2t, 2t+1 split row r0 + t
+  kWarpPerRow = 2,    // longer rows: warp w computes rows r0 + w, r0 + w + 16, ...
+  kBlockPerRow = 3,   // one row longer than kChunkNnz, streamed from global memory
 };
 
 // Device view of a CSR matrix with its chunk partition.
@@ -93,7 +96,7 @@ cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s);
 int solve_blocks_per_sm(bool mixed);   // occupancy of the persistent kernel
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
-// Shared-memory bytes of the staged product (one stage pair + scratch).
+// Shared-memory bytes of the streamed product (ring + scratch).
 size_t spmv_smem_bytes();
 
 }  // namespace cgk

@@ -27,8 +27,8 @@
 namespace cgk {
 
 // Leave the kernel after a failed wait: drain in-flight copies, record status.
-__device__ __forceinline__ void solve_fail(const SpmvSmem& sm, StagePipe& pp, const SolveParams& P) {
-  stage_drain(sm, pp, P.wait_limit_ns);
+__device__ __forceinline__ void solve_fail(const RingSmem& sm, RingState& rs, const SolveParams& P) {
+  ring_drain(sm, rs, P.wait_limit_ns);
   if (threadIdx.x == 0) {
     atomicExch(&P.ctrl->abort, 1);
     atomicExch(&P.ctrl->status, kETIMEOUT);
@@ -38,14 +38,16 @@ __device__ __forceinline__ void solve_fail(const SpmvSmem& sm, StagePipe& pp, co
 template <bool kMixed>
 __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const SpmvSmem sm{smem_raw};
+  const RingSmem sm{smem_raw};
   const DevCsr& A = P.A;
   const int bid = blockIdx.x;
+  const int tid = threadIdx.x;
   const int c0 = A.block_chunk[bid], c1 = A.block_chunk[bid + 1];
   const int row0 = A.chunk_row[c0], row1 = A.chunk_row[c1];
   const unsigned long long lim = P.wait_limit_ns;
-  double* red = sm.red();
   int32_t* flag = sm.flag();
+  double* sc = sm.scalars();  // broadcast slots for per-step scalars
+  FxScratch* fx = sm.fx();
   SolveCtrl* ctrl = P.ctrl;
   const double* __restrict__ b = P.b;
   double* __restrict__ x = P.x;
@@ -54,39 +56,31 @@ __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P
   double* __restrict__ q = P.q;
   float* __restrict__ p32 = P.p32;
   const int nb = gridDim.x;
+  const double* const no_next = nullptr;
+  const float* const no_next32 = nullptr;
+  (void)no_next32;
 
-  stage_init(sm);
-  StagePipe pp;
+  RingState rs;
+  ring_init(sm, rs, A, row0, row1);
   GridBarrier gb;
   int slot = 0;
   int site = 0;
 
-  // Grid-wide sum of one or two per-thread values, identical in every CTA:
-  // CTA partials go to partials[slot], a barrier, then every CTA adds the nb
-  // partials in block order.  Two slots alternate so that a fast CTA writing
-  // the next partials never overwrites ones a slow CTA is still reading.
-  auto allreduce2 = [&](double& v0, double& v1) -> bool {
-    block_sum2(v0, v1, red);
-    double* part = P.partials + static_cast<size_t>(slot) * nb * 2;
-    if (threadIdx.x == 0) {
-      part[2 * bid] = v0;
-      part[2 * bid + 1] = v1;
-    }
+  // Grid-wide sum of one value per thread, identical in every CTA.  Each CTA
+  // sums its threads in fixed point, publishes the result, and after a grid
+  // barrier every CTA sums the nb CTA values, again in fixed point (exact and
+  // order-independent, hence the same bits everywhere).  Two slots of
+  // partials alternate so that a fast CTA publishing the next sum never
+  // overwrites values a slow CTA is still reading.
+  auto allreduce = [&](double v, double& out) -> bool {
+    const double cta = fx_block_sum(v, fx);
+    double* part = P.partials + static_cast<size_t>(slot) * nb;
+    if (tid == 0) part[bid] = cta;
     if (!gb.sync(ctrl, lim, ++site, flag)) return false;
-    double s0 = 0.0, s1 = 0.0;
-    for (int j = threadIdx.x; j < nb; j += kBlock) {
-      s0 += __ldcg(part + 2 * j);
-      s1 += __ldcg(part + 2 * j + 1);
-    }
-    block_sum2(s0, s1, red);
-    v0 = s0;
-    v1 = s1;
+    const double mine = tid < nb ? __ldcg(part + tid) : 0.0;
+    out = fx_block_sum(mine, fx);
     slot ^= 1;
     return true;
-  };
-  auto allreduce = [&](double& v) -> bool {
-    double dummy = 0.0;
-    return allreduce2(v, dummy);
   };
 
   // ---- setup: r = b - A x, p = r, rho = r.r, ||b||^2
@@ -101,18 +95,17 @@ __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P
       acc_rr = fma(ri, ri, acc_rr);
       acc_bb = fma(bi, bi, acc_bb);
     };
-    if (!spmv_pass<double, double, double>(sm, pp, A, A.val, c0, c1, x, epi, lim)) {
-      solve_fail(sm, pp, P);
-      return;
-    }
+    bool ok;
+    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val32, lim);
+    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val, lim);
+    if (!ok) { solve_fail(sm, rs, P); return; }
   }
-  if (!allreduce2(acc_rr, acc_bb)) { solve_fail(sm, pp, P); return; }
-  double rho = acc_rr;
-  const double bnorm2 = acc_bb;
-  const double bnorm = sqrt(bnorm2);
+  double rho, bnorm2;
+  if (!allreduce(acc_rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, rs, P); return; }
   if (bnorm2 == 0.0) {  // b = 0: the solution is 0
-    for (int i = row0 + threadIdx.x; i < row1; i += kBlock) x[i] = 0.0;
-    if (bid == 0 && threadIdx.x == 0) {
+    ring_drain(sm, rs, lim);
+    for (int i = row0 + tid; i < row1; i += kBlock) x[i] = 0.0;
+    if (bid == 0 && tid == 0) {
       ctrl->status = kOK;
       ctrl->iters = 0;
       ctrl->rho = 0.0;
@@ -122,10 +115,12 @@ __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P
     }
     return;
   }
-  const double thresh = P.tol * bnorm;
+  // Stopping test sqrt(rho) <= tol ||b|| evaluated as rho <= tol^2 ||b||^2
+  // (no square root on the critical path; the same test up to rounding).
+  const double thresh2 = (P.tol * P.tol) * bnorm2;
   int64_t k = 0;
   int32_t status = kOK;
-  bool done = sqrt(rho) <= thresh;
+  bool done = rho <= thresh2;
 
   while (!done && k < P.maxit) {
     // ---- q = A p, gamma = p.q
@@ -137,119 +132,152 @@ __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P
         q[i] = qi;
         acc_g = fma(p[i], qi, acc_g);
       };
-      ok = spmv_pass<float, float, float>(sm, pp, A, A.val32, c0, c1, p32, epi, lim);
+      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, c0, c1, p32, epi, A.val32, lim);
     } else {
       auto epi = [&](int i, double s) {
         q[i] = s;
         acc_g = fma(p[i], s, acc_g);
       };
-      ok = spmv_pass<double, double, double>(sm, pp, A, A.val, c0, c1, p, epi, lim);
+      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, p, epi, A.val, lim);
     }
-    if (!ok || !allreduce(acc_g)) { solve_fail(sm, pp, P); return; }
-    const double gamma = acc_g;
+    double gamma;
+    if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, rs, P); return; }
     if (!(gamma > 0.0) || !isfinite(gamma)) {  // not SPD, or overflow
       status = kEBREAKDOWN;
       break;
     }
-    const double alpha = rho / gamma;
+    // alpha = rho / gamma, computed once and broadcast (FP64 division is slow)
+    if (tid == 0) sc[0] = rho / gamma;
+    __syncthreads();
+    const double alpha = sc[0];
 
-    // ---- r -= alpha q, rho' = r.r
+    // ---- r -= alpha q, rho' = r.r   (four rows per thread in flight)
     double acc_r = 0.0;
-    for (int i = row0 + threadIdx.x; i < row1; i += kBlock) {
-      const double ri = fma(-alpha, q[i], r[i]);
-      r[i] = ri;
-      acc_r = fma(ri, ri, acc_r);
+    for (int base = row0 + tid; base < row1; base += 4 * kBlock) {
+      double qv[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * kBlock;
+        if (i < row1) { qv[u] = q[i]; rv[u] = r[i]; }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * kBlock;
+        if (i < row1) {
+          const double rn = fma(-alpha, qv[u], rv[u]);
+          r[i] = rn;
+          acc_r = fma(rn, rn, acc_r);
+        }
+      }
     }
-    if (!allreduce(acc_r)) { solve_fail(sm, pp, P); return; }
-    double rho_new = acc_r;
+    double rho_new;
+    if (!allreduce(acc_r, rho_new)) { solve_fail(sm, rs, P); return; }
     ++k;
 
     bool replace = false;
-    if constexpr (kMixed)
-      replace = (P.replace_every > 0 && k % P.replace_every == 0) || sqrt(rho_new) <= thresh;
+    if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rho_new <= thresh2;
     if (replace) {
       // x += alpha p, then r = b - A x in FP64 (residual replacement)
-      for (int i = row0 + threadIdx.x; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
-      if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, pp, P); return; }
+      for (int i = row0 + tid; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
+      if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
       double acc_t = 0.0;
       auto epi = [&](int i, double s) {
         const double ri = b[i] - s;
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
       };
-      if (!spmv_pass<double, double, double>(sm, pp, A, A.val, c0, c1, x, epi, lim) || !allreduce(acc_t)) {
-        solve_fail(sm, pp, P);
+      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val32, lim) ||
+          !allreduce(acc_t, rho_new)) {
+        solve_fail(sm, rs, P);
         return;
       }
-      rho_new = acc_t;
-      if (sqrt(rho_new) <= thresh) {
+      if (rho_new <= thresh2) {
         rho = rho_new;
         done = true;
         break;
       }
-      const double beta = rho_new / rho;
-      for (int i = row0 + threadIdx.x; i < row1; i += kBlock) {
+      if (tid == 0) sc[1] = rho_new / rho;
+      __syncthreads();
+      const double beta = sc[1];
+      for (int i = row0 + tid; i < row1; i += kBlock) {
         const double pi = fma(beta, p[i], r[i]);
         p[i] = pi;
         if constexpr (kMixed) p32[i] = static_cast<float>(pi);
       }
       rho = rho_new;
     } else {
-      if (!kMixed && sqrt(rho_new) <= thresh) {
-        for (int i = row0 + threadIdx.x; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
+      if (!kMixed && rho_new <= thresh2) {
+        for (int i = row0 + tid; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
         rho = rho_new;
         done = true;
         break;
       }
       // ---- x += alpha p; p = r + beta p
-      const double beta = rho_new / rho;
-      for (int i = row0 + threadIdx.x; i < row1; i += kBlock) {
-        const double pi = p[i];
-        x[i] = fma(alpha, pi, x[i]);
-        const double pn = fma(beta, pi, r[i]);
-        p[i] = pn;
-        if constexpr (kMixed) p32[i] = static_cast<float>(pn);
+      if (tid == 0) sc[1] = rho_new / rho;
+      __syncthreads();
+      const double beta = sc[1];
+      for (int base = row0 + tid; base < row1; base += 4 * kBlock) {
+        double pv[4], rv[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kBlock;
+          if (i < row1) { pv[u] = p[i]; rv[u] = r[i]; xv[u] = x[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kBlock;
+          if (i < row1) {
+            x[i] = fma(alpha, pv[u], xv[u]);
+            const double pn = fma(beta, pv[u], rv[u]);
+            p[i] = pn;
+            if constexpr (kMixed) p32[i] = static_cast<float>(pn);
+          }
+        }
       }
       rho = rho_new;
     }
-    if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, pp, P); return; }
+    if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
   }
   if (status == kOK && !done) status = kENOTCONV;
 
   // ---- true residual ||b - A x|| / ||b|| (x complete everywhere first)
-  if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, pp, P); return; }
+  if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
   double acc_t = 0.0;
   {
     auto epi = [&](int i, double s) {
       const double d = b[i] - s;
       acc_t = fma(d, d, acc_t);
     };
-    if (!spmv_pass<double, double, double>(sm, pp, A, A.val, c0, c1, x, epi, lim) || !allreduce(acc_t)) {
-      solve_fail(sm, pp, P);
+    double tsum;
+    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, no_next, lim) ||
+        !allreduce(acc_t, tsum)) {
+      solve_fail(sm, rs, P);
       return;
     }
+    acc_t = tsum;
   }
-  if (bid == 0 && threadIdx.x == 0) {
+  if (bid == 0 && tid == 0) {
     ctrl->status = status;
     ctrl->iters = k;
     ctrl->rho = rho;
     ctrl->bnorm2 = bnorm2;
-    ctrl->relres_rec = sqrt(rho) / bnorm;
-    ctrl->relres_true = sqrt(acc_t) / bnorm;
+    ctrl->relres_rec = sqrt(rho / bnorm2);
+    ctrl->relres_true = sqrt(acc_t / bnorm2);
   }
 }
 
-// y = A x over the CTA's chunk range (same partition and staging as the solve).
+// y = A x over the CTA's chunk range (same partition and stream as the solve).
 __global__ void __launch_bounds__(kBlock, 1) spmv_kernel(const DevCsr A, const double* __restrict__ x,
                                                           double* __restrict__ y, int32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const SpmvSmem sm{smem_raw};
-  stage_init(sm);
-  StagePipe pp;
+  const RingSmem sm{smem_raw};
   const int c0 = A.block_chunk[blockIdx.x], c1 = A.block_chunk[blockIdx.x + 1];
+  RingState rs;
+  ring_init(sm, rs, A, A.chunk_row[c0], A.chunk_row[c1]);
   auto epi = [&](int i, double s) { y[i] = s; };
-  if (!spmv_pass<double, double, double>(sm, pp, A, A.val, c0, c1, x, epi, 2000000000ull)) {
-    stage_drain(sm, pp, 2000000000ull);
+  const double* const no_next = nullptr;
+  if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, no_next, 2000000000ull)) {
+    ring_drain(sm, rs, 2000000000ull);
     if (threadIdx.x == 0) atomicExch(err, kETIMEOUT);
   }
 }
@@ -271,25 +299,25 @@ cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
 }  // namespace
 
 cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* err, cudaStream_t s) {
-  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(spmv_kernel), SpmvSmem::kBytes);
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(spmv_kernel), RingSmem::kBytes);
   if (e != cudaSuccess) return e;
-  spmv_kernel<<<A.nblocks, kBlock, SpmvSmem::kBytes, s>>>(A, x, y, err);
+  spmv_kernel<<<A.nblocks, kBlock, RingSmem::kBytes, s>>>(A, x, y, err);
   return cudaGetLastError();
 }
 
-size_t spmv_smem_bytes() { return SpmvSmem::kBytes; }
+size_t spmv_smem_bytes() { return RingSmem::kBytes; }
 
 int solve_blocks_per_sm(bool mixed) {
   int nb = 0;
   cudaError_t e;
   if (mixed) {
-    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), SpmvSmem::kBytes);
+    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), RingSmem::kBytes);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<true>, kBlock, SpmvSmem::kBytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<true>, kBlock, RingSmem::kBytes);
   } else {
-    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), SpmvSmem::kBytes);
+    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), RingSmem::kBytes);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<false>, kBlock, SpmvSmem::kBytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<false>, kBlock, RingSmem::kBytes);
   }
   return e == cudaSuccess ? nb : -1;
 }
@@ -297,15 +325,15 @@ int solve_blocks_per_sm(bool mixed) {
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
   void* args[] = {const_cast<SolveParams*>(&P)};
   if (mixed) {
-    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), SpmvSmem::kBytes);
+    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), RingSmem::kBytes);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_solve_kernel<true>), dim3(P.A.nblocks),
-                                       dim3(kBlock), args, SpmvSmem::kBytes, s);
+                                       dim3(kBlock), args, RingSmem::kBytes, s);
   }
-  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), SpmvSmem::kBytes);
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), RingSmem::kBytes);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_solve_kernel<false>), dim3(P.A.nblocks),
-                                     dim3(kBlock), args, SpmvSmem::kBytes, s);
+                                     dim3(kBlock), args, RingSmem::kBytes, s);
 }
 
 // ---- self-test of the bounded wait: one CTA waits at a grid barrier that

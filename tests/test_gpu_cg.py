@@ -210,3 +210,19 @@ def test_wait_timeout_selftest_then_context_usable():
     with handle(A) as h:
         res, x = solve(h, b)
     assert res.status == cg.CG_OK
+
+
+@pytest.mark.parametrize("every", [1, 3])
+def test_mixed_frequent_replacement(every):
+    """Residual replacement every 1 or 3 steps switches the product between the
+    FP32 and FP64 matrix copies nearly every step."""
+    cg = cg_mod()
+    A = fi.q1(10, 1.0, 9)
+    b = oracle.spmv(A, fi.xstar(9, A.n))
+    with handle(A, precision=cg.CG_PREC_MIXED, replace_every=every) as h:
+        res, x = solve(h, b, maxit=10 * A.n)
+    assert res.status == cg.CG_OK, res
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 * 1.0000001
+    refmx = oracle.cg_mixed(A, b, tol=1e-10, replace_every=every)
+    assert abs(res.iters - refmx.iters) <= max(5, 0.05 * refmx.iters), (res.iters, refmx.iters)

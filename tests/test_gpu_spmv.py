@@ -157,3 +157,15 @@ def test_invalid_device_csr_rejected():
     with pytest.raises(cg.CGError) as e:
         cg.cg_create(rp, ci, va)
     assert e.value.status == cg.CG_EINVAL
+
+
+def test_rows_longer_than_the_ring():
+    """Rows of 8193 .. 39000 entries (longer than a chunk, some longer than the
+    whole shared-memory ring) next to short rows; integer data -> exact."""
+    A = fi.random_csr(40000, 3, 0, 20, empty_frac=0.1, long_rows=(17000, 30000, 39000, 8193, 8192), integer=True)
+    x = np.round(fi.uniform(3, 5, A.n, -9, 9))
+    with handle(A) as h:
+        y = gpu_spmv(h, x)
+        y2 = gpu_spmv(h, x)
+    assert np.array_equal(y, oracle.spmv(A, x))
+    assert np.array_equal(y, y2)
