@@ -402,16 +402,20 @@ __device__ __forceinline__ void ring_drain(const RingSmem& sm, RingState& rs, un
 template <typename T, typename X, typename Acc, int U>
 __device__ __forceinline__ Acc seg_dot(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
   Acc s = Acc(0);
-  if (len <= U) {
+  // Called by all 32 lanes of the warp (len = 0 for lanes without a row).
+  // The unroll bound is the warp's longest segment, so no FP64 instruction is
+  // issued for a slot that no lane needs: FP64 issue is the scarce resource.
+  const int wmax = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(len)));
+  if (wmax <= U) {
     // all gathers first (only they have long latency), then the FMAs with
     // the values read from shared memory as they are consumed
     X xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
+      if (u < wmax && u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
+      if (u < wmax && u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
     return s;
   }
   int t = 0;
@@ -439,21 +443,24 @@ __device__ __forceinline__ void chunk_compute_ring(const RingSmem& sm, int mode,
   const int32_t* rc = sm.col();
   if (mode == kThreadPerRow) {
     const int i = r0 + static_cast<int>(threadIdx.x);
+    int ks = 0, len = 0;
     if (i < r1) {
-      const int ks = row_ptr[i], ke = row_ptr[i + 1];
-      epi(i, seg_dot<T, X, Acc, 16>(rv, rc, ks - kb + off, ke - ks, x));
+      ks = row_ptr[i];
+      len = row_ptr[i + 1] - ks;
     }
+    const Acc s = seg_dot<T, X, Acc, 16>(rv, rc, ks - kb + off, len, x);
+    if (i < r1) epi(i, s);
   } else if (mode == kPairPerRow) {
     const int i = r0 + static_cast<int>(threadIdx.x >> 1);
     const int h = threadIdx.x & 1;
-    Acc part = Acc(0);
+    int a = 0, len = 0;
     if (i < r1) {
       const int ks = row_ptr[i], ke = row_ptr[i + 1];
       const int half = (ke - ks + 1) >> 1;
-      const int a = h ? ks + half : ks;
-      const int len = h ? (ke - ks - half) : half;
-      part = seg_dot<T, X, Acc, 16>(rv, rc, a - kb + off, len, x);
+      a = h ? ks + half : ks;
+      len = h ? (ke - ks - half) : half;
     }
+    const Acc part = seg_dot<T, X, Acc, 16>(rv, rc, a - kb + off, len, x);
     // first half + second half: the same value in both lanes (commutative add)
     const Acc other = __shfl_xor_sync(0xffffffffu, part, 1);
     const Acc s = part + other;

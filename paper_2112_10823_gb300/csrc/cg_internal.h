@@ -6,8 +6,11 @@
 
 namespace cgk {
 
-// The persistent kernels run one 512-thread CTA per SM.
-constexpr int kBlock = 512;
+// The persistent kernels run two 256-thread CTAs per SM: two independent
+// instruction streams whose memory-latency phases overlap each other's FP64
+// phases.
+constexpr int kBlock = 256;
+constexpr int kCtasPerSm = 2;
 constexpr int kWarps = kBlock / 32;
 
 // Matrix stream of a CTA: its CSR values and column indices flow through a
@@ -15,8 +18,8 @@ constexpr int kWarps = kBlock / 32;
 // of 1-D TMA bulk copies completing on the slot's mbarrier.
 constexpr int kPieceLog = 11;
 constexpr int kPiece = 1 << kPieceLog;  // 2048 entries
-constexpr int kSlots = 8;
-constexpr int kRing = kPiece * kSlots;  // 16384 entries: 128 KB of FP64 values + 64 KB of indices
+constexpr int kSlots = 4;
+constexpr int kRing = kPiece * kSlots;  // 8192 entries: 64 KB of FP64 values + 32 KB of indices
 constexpr int kRingMask = kRing - 1;
 // A compute chunk is a run of consecutive rows computed together: at most
 // kChunkNnz entries (half the ring, so the next pieces stream in meanwhile)
@@ -31,7 +34,7 @@ constexpr int kPadEntries = 8;
 enum ChunkMode : int32_t {
   kThreadPerRow = 0,  // rows of <= 16 entries: thread t computes row r0 + t
   kPairPerRow = 1,    // rows of <= 64 entries: threads 2t, 2t+1 split row r0 + t
-  kWarpPerRow = 2,    // longer rows: warp w computes rows r0 + w, r0 + w + 16, ...
+  kWarpPerRow = 2,    // longer rows: warp w computes rows r0 + w, r0 + w + 8, ...
   kBlockPerRow = 3,   // one row longer than kChunkNnz, streamed from global memory
 };
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ void solve_fail(const RingSmem& sm, RingState& rs, co
 }
 
 template <bool kMixed>
-__global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P) {
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
   const DevCsr& A = P.A;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kBlock, 1) cg_solve_kernel(const SolveParams P
 }
 
 // y = A x over the CTA's chunk range (same partition and stream as the solve).
-__global__ void __launch_bounds__(kBlock, 1) spmv_kernel(const DevCsr A, const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A, const double* __restrict__ x,
                                                           double* __restrict__ y, int32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
