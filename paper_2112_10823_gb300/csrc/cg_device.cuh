@@ -116,24 +116,34 @@ struct FxScratch {
   double result;
 };
 
-// Sum over the CTA of one double per thread, exactly in fixed point.
+// Sum over the CTA of K doubles per thread, exactly in fixed point.
 //
 // FP64 adds cost 64 cycles of latency each on this GPU, so a tree of them over
-// 512 values sits on the critical path of every CG step.  Instead each value is
-// rounded to a common fixed-point grid set by the largest exponent E in the
-// CTA (spacing 2^(E-1074), i.e. about 2^-51 of the largest value, leaving 10
-// bits of headroom for up to 1024 terms), the integers are added exactly with
-// integer adds (order-independent, so the sum is deterministic whatever the
-// order of arrival), and the total is rounded once back to FP64.  Zero and
-// subnormal values count as zero; an infinite or NaN value makes the sum NaN.
-// Thread 0 converts the total; every thread receives it through shared memory.
-// Requires blockDim.x == kBlock.
-__device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
+// hundreds of values sits on the critical path of every CG step.  Instead each
+// value is rounded to a common fixed-point grid set by the largest exponent E
+// among all values (spacing 2^(E-1074), i.e. about 2^-51 of the largest value,
+// leaving 10 bits of headroom for up to 1024 terms), the integers are added
+// exactly with integer adds (order-independent, so the sum is deterministic
+// whatever the order of arrival), and the total is rounded once back to FP64.
+// Zero and subnormal values count as zero; an infinite or NaN value makes the
+// sum NaN.  Thread 0 converts the total; every thread receives it through
+// shared memory.  Requires blockDim.x == kBlock and K * kBlock <= 1024.
+template <int K>
+__device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* sc) {
+  static_assert(K * kBlock <= 1024, "fixed-point headroom is 10 bits");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int e = static_cast<int>((bits >> 52) & 0x7ffull);
-  const unsigned int ew = __reduce_max_sync(0xffffffffu, static_cast<unsigned int>(e));
-  const int nfw = __any_sync(0xffffffffu, e == 0x7ff);
+  unsigned long long bits[K];
+  int e[K];
+  int emax = 0, nfl = 0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    bits[j] = static_cast<unsigned long long>(__double_as_longlong(v[j]));
+    e[j] = static_cast<int>((bits[j] >> 52) & 0x7ffull);
+    emax = max(emax, e[j]);
+    nfl |= (e[j] == 0x7ff);
+  }
+  const unsigned int ew = __reduce_max_sync(0xffffffffu, static_cast<unsigned int>(emax));
+  const int nfw = __any_sync(0xffffffffu, nfl);
   __syncthreads();  // earlier users of sc are done
   if (lane == 0) {
     sc->e[warp] = static_cast<int32_t>(ew);
@@ -147,12 +157,15 @@ __device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
     nf |= sc->nf[w];
   }
   long long m = 0;
-  if (e != 0 && !nf) {
-    const int s = E - e + 1;  // >= 1
-    if (s < 64) {
-      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const unsigned long long rnd = (M + (1ull << (s - 1))) >> s;
-      m = (bits >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (e[j] != 0 && !nf) {
+      const int s = E - e[j] + 1;  // >= 1
+      if (s < 64) {
+        const unsigned long long M = (bits[j] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const unsigned long long rnd = (M + (1ull << (s - 1))) >> s;
+        m += (bits[j] >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+      }
     }
   }
 #pragma unroll
@@ -171,6 +184,11 @@ __device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
   }
   __syncthreads();
   return sc->result;
+}
+
+__device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
+  const double a[1] = {v};
+  return fx_block_sum<1>(a, sc);
 }
 
 // ------------------------------------------------------------ grid barrier

@@ -35,6 +35,9 @@ __device__ __forceinline__ void solve_fail(const RingSmem& sm, RingState& rs, co
   }
 }
 
+// CTA sums each thread reads in the grid-wide sum: nblocks <= kMaxCtaSums * kBlock.
+constexpr int kMaxCtaSums = 4;
+
 template <bool kMixed>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -77,8 +80,14 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     double* part = P.partials + static_cast<size_t>(slot) * nb;
     if (tid == 0) part[bid] = cta;
     if (!gb.sync(ctrl, lim, ++site, flag)) return false;
-    const double mine = tid < nb ? __ldcg(part + tid) : 0.0;
-    out = fx_block_sum(mine, fx);
+    // every CTA sums all nb CTA values (up to kMaxCtaSums per thread)
+    double mine[kMaxCtaSums];
+#pragma unroll
+    for (int j = 0; j < kMaxCtaSums; ++j) {
+      const int c = tid + j * kBlock;
+      mine[j] = c < nb ? __ldcg(part + c) : 0.0;
+    }
+    out = fx_block_sum<kMaxCtaSums>(mine, fx);
     slot ^= 1;
     return true;
   };
