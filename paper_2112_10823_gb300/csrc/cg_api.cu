@@ -3,6 +3,7 @@
 // memory ownership, and the launch + read-back of each call.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,15 +26,16 @@ struct cg_ctx {
   int64_t n = 0, nnz = 0;
   int num_sms = 0;
   int nblocks = 0;
-  int nchunks = 0;
+  int nsteps = 0;
   // device memory owned by the handle
   int32_t* d_row_ptr = nullptr;
   int32_t* d_col = nullptr;
   double* d_val = nullptr;
   float* d_val32 = nullptr;
-  int32_t* d_chunk_row = nullptr;
-  int32_t* d_chunk_mode = nullptr;
-  int32_t* d_block_chunk = nullptr;
+  int4* d_step = nullptr;
+  int32_t* d_step_mode = nullptr;
+  int32_t* d_warp_step = nullptr;
+  int32_t* d_block_row = nullptr;
   double* d_r = nullptr;
   double* d_p = nullptr;
   double* d_q = nullptr;
@@ -98,62 +100,89 @@ bool is_device_ptr(const void* p) {
 }
 
 // Row partition of the persistent kernels.  Rows are split into `nblocks`
-// contiguous ranges of about equal cost (stored entries + kRowCost per row,
-// the per-row vector work), and each range into compute chunks of at most
-// kChunkNnz entries.  A chunk whose rows all hold <= 16 entries is computed
-// one thread per row (<= kBlock rows); rows of <= 64 entries two threads per
-// row (<= kBlock/2 rows); longer rows one warp per row.  A row longer than
-// kChunkNnz is a chunk alone, streamed from global memory.
+// contiguous CTA ranges of about equal cost (stored entries + kRowCost per
+// row, the per-row vector work), each CTA range into kWarps warp ranges the
+// same way, and each warp range into steps (see cg_internal.h): up to 32 rows
+// of <= 16 entries, up to 16 rows of <= 64 entries, or segments of <= kSegNnz
+// entries of a longer row, never more than kStepNnz entries per step.  Two
+// sentinel steps follow the last one (the kernels read descriptors ahead).
 constexpr int64_t kRowCost = 6;
 
-int chunk_mode_for(int64_t maxlen) {
-  return maxlen <= 16 ? cgk::kThreadPerRow : (maxlen <= 64 ? cgk::kPairPerRow : cgk::kWarpPerRow);
-}
-int64_t chunk_row_cap(int mode) { return mode == cgk::kPairPerRow ? cgk::kBlock / 2 : cgk::kBlock; }
+struct Partition {
+  std::vector<int4> step;
+  std::vector<int32_t> step_mode;
+  std::vector<int32_t> warp_step;
+  std::vector<int32_t> block_row;
+};
 
-void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, std::vector<int32_t>& chunk_row,
-                     std::vector<int32_t>& chunk_mode, std::vector<int32_t>& block_chunk) {
-  chunk_row.clear();
-  chunk_mode.clear();
-  block_chunk.assign(static_cast<size_t>(nblocks) + 1, 0);
-  const int64_t total = static_cast<int64_t>(rp[n]) + kRowCost * n;
-  int64_t row = 0;
-  for (int b = 0; b < nblocks; ++b) {
-    block_chunk[b] = static_cast<int32_t>(chunk_row.size());
-    // end of this block's range: first row i with cost(0, i) >= total * (b+1) / nblocks
-    const int64_t goal = (b == nblocks - 1) ? total : (total * (b + 1)) / nblocks;
-    int64_t lo = row, hi = n;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) / 2;
-      if (static_cast<int64_t>(rp[mid]) + kRowCost * mid >= goal) hi = mid;
-      else lo = mid + 1;
+int64_t cost_split(const std::vector<int32_t>& rp, int64_t lo_row, int64_t hi_row, int64_t part, int64_t parts) {
+  // first row i in [lo_row, hi_row] with cost(lo_row, i) >= cost(lo_row, hi_row) * part / parts
+  const int64_t c0 = static_cast<int64_t>(rp[lo_row]) + kRowCost * lo_row;
+  const int64_t c1 = static_cast<int64_t>(rp[hi_row]) + kRowCost * hi_row;
+  const int64_t goal = c0 + ((c1 - c0) * part) / parts;
+  int64_t lo = lo_row, hi = hi_row;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (static_cast<int64_t>(rp[mid]) + kRowCost * mid >= goal) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partition& P) {
+  while (row < end) {
+    const int64_t len0 = rp[row + 1] - rp[row];
+    if (len0 > 64) {  // a long row: segments through the ring
+      for (int64_t e = rp[row]; e < rp[row + 1]; e += cgk::kSegNnz) {
+        const int64_t e1 = std::min<int64_t>(e + cgk::kSegNnz, rp[row + 1]);
+        int32_t m = cgk::kSegment;
+        if (e == rp[row]) m |= cgk::kSegFirst;
+        if (e1 == rp[row + 1]) m |= cgk::kSegLast;
+        P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), static_cast<int>(e),
+                                   static_cast<int>(e1)));
+        P.step_mode.push_back(m);
+      }
+      ++row;
+      continue;
     }
-    const int64_t end = (b == nblocks - 1) ? n : lo;
+    const int64_t start = row;
+    int64_t cnt = 0, maxlen = 0;
     while (row < end) {
-      const int64_t len0 = rp[row + 1] - rp[row];
-      if (len0 > cgk::kChunkNnz) {
-        chunk_row.push_back(static_cast<int32_t>(row));
-        chunk_mode.push_back(cgk::kBlockPerRow);
-        ++row;
-        continue;
-      }
-      const int64_t start = row;
-      int64_t cnt = 0, maxlen = 0;
-      while (row < end) {
-        const int64_t len = rp[row + 1] - rp[row];
-        if (len > cgk::kChunkNnz || cnt + len > cgk::kChunkNnz) break;
-        const int64_t newmax = len > maxlen ? len : maxlen;
-        if (row - start + 1 > chunk_row_cap(chunk_mode_for(newmax))) break;
-        cnt += len;
-        maxlen = newmax;
-        ++row;
-      }
-      chunk_row.push_back(static_cast<int32_t>(start));
-      chunk_mode.push_back(chunk_mode_for(maxlen));
+      const int64_t len = rp[row + 1] - rp[row];
+      if (len > 64 || cnt + len > cgk::kStepNnz) break;
+      const int64_t nm = std::max(maxlen, len);
+      const int64_t cap = nm <= 16 ? 32 : 16;
+      if (row - start + 1 > cap) break;
+      cnt += len;
+      maxlen = nm;
+      ++row;
+    }
+    P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
+    P.step_mode.push_back(maxlen <= 16 ? cgk::kLanePerRow : cgk::kPairPerRow);
+  }
+}
+
+void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P) {
+  P.step.clear();
+  P.step_mode.clear();
+  P.warp_step.assign(static_cast<size_t>(nblocks) * cgk::kWarps + 1, 0);
+  P.block_row.assign(static_cast<size_t>(nblocks) + 1, 0);
+  for (int b = 0; b <= nblocks; ++b) P.block_row[b] = static_cast<int32_t>(cost_split(rp, 0, n, b, nblocks));
+  P.block_row[nblocks] = static_cast<int32_t>(n);
+  for (int b = 0; b < nblocks; ++b) {
+    const int64_t r0 = P.block_row[b], r1 = P.block_row[b + 1];
+    for (int w = 0; w < cgk::kWarps; ++w) {
+      P.warp_step[static_cast<size_t>(b) * cgk::kWarps + w] = static_cast<int32_t>(P.step.size());
+      const int64_t a = cost_split(rp, r0, r1, w, cgk::kWarps);
+      const int64_t z = (w == cgk::kWarps - 1) ? r1 : cost_split(rp, r0, r1, w + 1, cgk::kWarps);
+      warp_steps(rp, a, z, P);
     }
   }
-  block_chunk[nblocks] = static_cast<int32_t>(chunk_row.size());
-  chunk_row.push_back(static_cast<int32_t>(n));
+  P.warp_step[static_cast<size_t>(nblocks) * cgk::kWarps] = static_cast<int32_t>(P.step.size());
+  for (int t = 0; t < 2; ++t) {  // sentinels
+    P.step.push_back(make_int4(static_cast<int>(n), static_cast<int>(n), rp[n], rp[n]));
+    P.step_mode.push_back(cgk::kLanePerRow);
+  }
 }
 
 cgk::DevCsr dev_view(const cg_ctx* h) {
@@ -162,11 +191,12 @@ cgk::DevCsr dev_view(const cg_ctx* h) {
   A.col_idx = h->d_col;
   A.val = h->d_val;
   A.val32 = h->d_val32;
-  A.chunk_row = h->d_chunk_row;
-  A.chunk_mode = h->d_chunk_mode;
-  A.block_chunk = h->d_block_chunk;
+  A.step = h->d_step;
+  A.step_mode = h->d_step_mode;
+  A.warp_step = h->d_warp_step;
+  A.block_row = h->d_block_row;
   A.n = static_cast<int32_t>(h->n);
-  A.nchunks = h->nchunks;
+  A.nsteps = h->nsteps;
   A.nblocks = h->nblocks;
   A.nnz = h->nnz;
   return A;
@@ -307,17 +337,18 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     return rc;
   }
 
-  std::vector<int32_t> chunk_row, chunk_mode, block_chunk;
-  build_partition(rp, n, h->nblocks, chunk_row, chunk_mode, block_chunk);
-  h->nchunks = static_cast<int>(chunk_mode.size());
+  Partition part;
+  build_partition(rp, n, h->nblocks, part);
+  h->nsteps = static_cast<int>(part.step.size()) - 2;
 
   const size_t pad = cgk::kPadEntries;
   CG_TRY(dalloc(h, &h->d_row_ptr, n + 1), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_col, nnz + pad), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_val, nnz + pad), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_chunk_row, chunk_row.size()), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_chunk_mode, chunk_mode.size() + 1), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_block_chunk, block_chunk.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_step, part.step.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_step_mode, part.step_mode.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_warp_step, part.warp_step.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_block_row, part.block_row.size()), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_r, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_p, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_q, n), "cg_create: cudaMalloc");
@@ -347,13 +378,15 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
                       csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice),
            "cg_create: upload");
   }
-  CG_TRY(cudaMemcpy(h->d_chunk_row, chunk_row.data(), sizeof(int32_t) * chunk_row.size(), cudaMemcpyHostToDevice),
+  CG_TRY(cudaMemcpy(h->d_step, part.step.data(), sizeof(int4) * part.step.size(), cudaMemcpyHostToDevice),
          "cg_create: upload");
-  if (!chunk_mode.empty())
-    CG_TRY(cudaMemcpy(h->d_chunk_mode, chunk_mode.data(), sizeof(int32_t) * chunk_mode.size(),
-                      cudaMemcpyHostToDevice),
-           "cg_create: upload");
-  CG_TRY(cudaMemcpy(h->d_block_chunk, block_chunk.data(), sizeof(int32_t) * block_chunk.size(),
+  CG_TRY(cudaMemcpy(h->d_step_mode, part.step_mode.data(), sizeof(int32_t) * part.step_mode.size(),
+                    cudaMemcpyHostToDevice),
+         "cg_create: upload");
+  CG_TRY(cudaMemcpy(h->d_warp_step, part.warp_step.data(), sizeof(int32_t) * part.warp_step.size(),
+                    cudaMemcpyHostToDevice),
+         "cg_create: upload");
+  CG_TRY(cudaMemcpy(h->d_block_row, part.block_row.data(), sizeof(int32_t) * part.block_row.size(),
                     cudaMemcpyHostToDevice),
          "cg_create: upload");
   CG_TRY(cudaMemset(h->d_dot_counter, 0, 16), "cg_create: memset");

@@ -249,14 +249,14 @@ struct GridBarrier {
 
 // ------------------------------------------------------ streamed CSR product
 
-// Shared memory of the streamed product: the value ring (sized for FP64; the
-// FP32 product uses its first half), the column-index ring, one mbarrier per
-// ring slot, reduction scratch and a few broadcast words.
+// Shared memory of a CTA: one ring per warp (values sized for FP64, the FP32
+// product uses the first half of a warp's value ring), the column-index
+// rings, kSlots mbarriers per warp, reduction scratch and broadcast words.
 struct RingSmem {
-  static constexpr size_t kValBytes = sizeof(double) * kRing;
-  static constexpr size_t kColBytes = sizeof(int32_t) * kRing;
+  static constexpr size_t kValBytes = sizeof(double) * kRing * kWarps;
+  static constexpr size_t kColBytes = sizeof(int32_t) * kRing * kWarps;
   static constexpr size_t kBarOff = kValBytes + kColBytes;
-  static constexpr size_t kRedOff = kBarOff + 8 * kSlots;
+  static constexpr size_t kRedOff = kBarOff + 8 * kSlots * kWarps;
   static constexpr size_t kRedBytes = sizeof(double) * (kBlock + 8);
   static constexpr size_t kFxOff = kRedOff + kRedBytes;
   static constexpr size_t kFxBytes = (sizeof(FxScratch) + 15) & ~size_t(15);
@@ -265,22 +265,25 @@ struct RingSmem {
 
   unsigned char* base;
   template <typename T>
-  __device__ T* val() const { return reinterpret_cast<T*>(base); }
-  __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + kValBytes); }
-  __device__ uint64_t* bar(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + s; }
+  __device__ T* val(int w) const { return reinterpret_cast<T*>(base + sizeof(double) * kRing * w); }
+  __device__ int32_t* col(int w) const { return reinterpret_cast<int32_t*>(base + kValBytes) + kRing * w; }
+  __device__ uint64_t* bar(int w, int s) const {
+    return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots * w + s;
+  }
   __device__ double* red() const { return reinterpret_cast<double*>(base + kRedOff); }
   __device__ FxScratch* fx() const { return reinterpret_cast<FxScratch*>(base + kFxOff); }
   __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + kMiscOff); }
   __device__ double* scalars() const { return reinterpret_cast<double*>(base + kMiscOff + 16); }
 };
 
-// Per-CTA state of the matrix stream; in registers, uniform across the CTA.
-// Pieces are numbered globally (across passes) so that the slot of a piece is
-// (global number % kSlots) and its mbarrier phase (global number / kSlots) & 1.
-struct RingState {
-  int kb = 0;            // first entry of the CTA's range, rounded down to a multiple of 4
-  int ke = 0;            // end of the CTA's entry range
+// State of one warp's matrix stream; in registers, identical in all lanes.
+// Pieces are numbered globally (across passes): the slot of global piece g
+// is g % kSlots and the mbarrier phase it completes is (g / kSlots) & 1.
+struct WarpStream {
+  int kb = 0;            // first entry of the warp's range, rounded down to a multiple of 4
+  int ke = 0;            // end of the warp's entry range
   int npieces = 0;       // pieces per pass
+  int s0 = 0, s1 = 0;    // the warp's steps [s0, s1)
   uint32_t gbase = 0;    // global number of piece 0 of the current pass
   int issued = 0;        // pieces of the current pass issued
   int waited = 0;        // pieces of the current pass seen complete
@@ -289,144 +292,136 @@ struct RingState {
   int pre_count = 0;     // pieces of the next pass already issued
 };
 
-__device__ __forceinline__ void ring_init(const RingSmem& sm, RingState& rs, const DevCsr& A, int row0,
-                                          int row1) {
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(sm.bar(s), 1);
-    fence_mbar_init();
-  }
+// Set up the rings of all warps (all threads call) and this warp's stream.
+__device__ __forceinline__ void stream_init(const RingSmem& sm, WarpStream& ws, const DevCsr& A) {
+  const int w = threadIdx.x >> 5;
+  if (threadIdx.x < kWarps * kSlots) mbar_init(sm.bar(threadIdx.x / kSlots, threadIdx.x % kSlots), 1);
+  if (threadIdx.x == 0) fence_mbar_init();
   __syncthreads();
-  rs.kb = A.row_ptr[row0] & ~3;
-  rs.ke = A.row_ptr[row1];
-  // a CTA without rows streams nothing (kb may sit below ke after rounding)
-  rs.npieces = row1 > row0 ? (rs.ke - rs.kb + kPiece - 1) >> kPieceLog : 0;
+  const int gw = blockIdx.x * kWarps + w;
+  ws.s0 = A.warp_step[gw];
+  ws.s1 = A.warp_step[gw + 1];
+  if (ws.s1 > ws.s0) {
+    ws.kb = A.step[ws.s0].z & ~3;
+    ws.ke = A.step[ws.s1 - 1].w;
+    ws.npieces = (ws.ke - ws.kb + kPiece - 1) >> kPieceLog;
+  }
 }
 
-// Ring position of the first entry of piece 0 of the pass starting at gbase.
-__device__ __forceinline__ int ring_pos_of_piece0(uint32_t gbase) {
-  return static_cast<int>((gbase % kSlots) * kPiece);
-}
-
-// Issue piece j of the pass starting at gbase (values of type T).  One thread.
+// Issue piece j of the pass starting at gbase (values of type T).  Lane 0.
 template <typename T>
-__device__ __forceinline__ void ring_issue(const RingSmem& sm, const RingState& rs, uint32_t gbase, int j,
-                                           const T* val, const int32_t* col) {
-  const int e0 = rs.kb + j * kPiece;
+__device__ __forceinline__ void stream_issue(const RingSmem& sm, const WarpStream& ws, uint32_t gbase, int j,
+                                             const T* val, const int32_t* col) {
+  const int w = threadIdx.x >> 5;
+  const int e0 = ws.kb + j * kPiece;
   int e1 = e0 + kPiece;
-  const int ke4 = (rs.ke + 3) & ~3;  // copy whole 16-byte groups (<= 3 padding entries)
+  const int ke4 = (ws.ke + 3) & ~3;  // whole 16-byte groups (<= 3 padding entries)
   if (e1 > ke4) e1 = ke4;
   const int slot = static_cast<int>((gbase + static_cast<uint32_t>(j)) % kSlots);
   const int pos = slot * kPiece;
   const uint32_t bv = static_cast<uint32_t>(e1 - e0) * sizeof(T);
   const uint32_t bc = static_cast<uint32_t>(e1 - e0) * 4u;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(sm.bar(slot), bv + bc);
-  bulk_g2s(sm.val<T>() + pos, val + e0, bv, sm.bar(slot));
-  bulk_g2s(sm.col() + pos, col + e0, bc, sm.bar(slot));
+  mbar_arrive_expect_tx(sm.bar(w, slot), bv + bc);
+  bulk_g2s(sm.val<T>(w) + pos, val + e0, bv, sm.bar(w, slot));
+  bulk_g2s(sm.col(w) + pos, col + e0, bc, sm.bar(w, slot));
 }
 
-// Wait (bounded) for global piece g; returns false if the wait gave up.
-__device__ __forceinline__ bool ring_wait_global(const RingSmem& sm, uint32_t g, unsigned long long limit_ns) {
+// Wait (bounded) for global piece g of this warp; uniform over the warp.
+__device__ __forceinline__ bool stream_wait_global(const RingSmem& sm, uint32_t g, unsigned long long limit_ns) {
+  const int w = threadIdx.x >> 5;
   const int slot = static_cast<int>(g % kSlots);
   const uint32_t parity = (g / kSlots) & 1u;
   uint32_t spins = 0;
   unsigned long long t0 = 0;
-  while (!mbar_try_wait(sm.bar(slot), parity)) {
+  int ok = 1;
+  while (!mbar_try_wait(sm.bar(w, slot), parity)) {
     if ((++spins & 63u) == 0) {
       const unsigned long long now = global_timer_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > limit_ns) return false;
+      else if (now - t0 > limit_ns) { ok = 0; break; }
     }
   }
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+__device__ __forceinline__ bool stream_wait_upto(const RingSmem& sm, WarpStream& ws, int upto,
+                                                 unsigned long long limit_ns) {
+  for (; ws.waited < upto; ++ws.waited)
+    if (!stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(ws.waited), limit_ns)) return false;
   return true;
 }
 
-// Wait for pieces [rs.waited, upto) of the current pass, in order.  Called by
-// all threads; the outcome is made uniform over the CTA.
-__device__ __forceinline__ bool ring_wait_upto(const RingSmem& sm, RingState& rs, int upto,
-                                               unsigned long long limit_ns) {
-  int ok = 1;
-  for (int j = rs.waited; j < upto; ++j)
-    if (!ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns)) ok = 0;
-  if (upto > rs.waited) rs.waited = upto;
-  return __syncthreads_and(ok) != 0;
-}
-
-// Keep the ring full: issue pieces while slots are free.  Thread 0 issues;
-// the counters advance in every thread.
+// Keep the warp's ring full.  The lanes of the warp must be done reading the
+// released slots (a __syncwarp precedes every call).
 template <typename T>
-__device__ __forceinline__ void ring_fill(const RingSmem& sm, RingState& rs, const T* val, const int32_t* col) {
-  int lim = rs.released + kSlots;
-  if (lim > rs.npieces) lim = rs.npieces;
-  if (threadIdx.x == 0)
-    for (int j = rs.issued; j < lim; ++j) ring_issue<T>(sm, rs, rs.gbase, j, val, col);
-  if (lim > rs.issued) rs.issued = lim;
+__device__ __forceinline__ void stream_fill(const RingSmem& sm, WarpStream& ws, const T* val, const int32_t* col) {
+  int lim = ws.released + kSlots;
+  if (lim > ws.npieces) lim = ws.npieces;
+  if ((threadIdx.x & 31) == 0)
+    for (int j = ws.issued; j < lim; ++j) stream_issue<T>(sm, ws, ws.gbase, j, val, col);
+  if (lim > ws.issued) ws.issued = lim;
 }
 
-// Start a pass over values of type T: adopt the pieces prefetched for it, or
+// Start a pass over values of type T: adopt pieces prefetched for it, or
 // first wait out prefetched pieces of the other type and skip past them.
 template <typename T>
-__device__ __forceinline__ bool ring_begin_pass(const RingSmem& sm, RingState& rs, const T* val,
-                                                const int32_t* col, unsigned long long limit_ns) {
-  if (rs.pre_count > 0 && rs.pre_type != static_cast<int>(sizeof(T))) {
-    int ok = 1;
-    for (int j = 0; j < rs.pre_count; ++j)
-      if (!ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns)) ok = 0;
-    if (!__syncthreads_and(ok)) return false;
-    rs.gbase += static_cast<uint32_t>(rs.pre_count);
-    rs.pre_count = 0;
+__device__ __forceinline__ bool stream_begin_pass(const RingSmem& sm, WarpStream& ws, const T* val,
+                                                  const int32_t* col, unsigned long long limit_ns) {
+  if (ws.pre_count > 0 && ws.pre_type != static_cast<int>(sizeof(T))) {
+    for (int j = 0; j < ws.pre_count; ++j)
+      if (!stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns)) return false;
+    ws.gbase += static_cast<uint32_t>(ws.pre_count);
+    ws.pre_count = 0;
   }
-  rs.issued = rs.pre_count;
-  rs.waited = 0;
-  rs.released = 0;
-  rs.pre_count = 0;
-  rs.pre_type = 0;
-  __syncthreads();  // no thread still reads the ring from an earlier pass
-  ring_fill<T>(sm, rs, val, col);
+  ws.issued = ws.pre_count;
+  ws.waited = 0;
+  ws.released = 0;
+  ws.pre_count = 0;
+  ws.pre_type = 0;
+  __syncwarp();
+  stream_fill<T>(sm, ws, val, col);
   return true;
 }
 
-// End a pass: every piece of it has been consumed.  Optionally issue the
-// first pieces of the next pass (values of type Tn) so that they load during
-// whatever the CTA does before that pass.
+// End a pass (all its pieces consumed); optionally issue the first pieces of
+// the next pass (values of type Tn) so they load during what follows.
 template <typename Tn>
-__device__ __forceinline__ void ring_end_pass(const RingSmem& sm, RingState& rs, const Tn* next_val,
-                                              const int32_t* col) {
-  rs.gbase += static_cast<uint32_t>(rs.npieces);
-  rs.issued = rs.waited = rs.released = 0;
-  rs.pre_count = 0;
-  rs.pre_type = 0;
-  if (next_val != nullptr && rs.npieces > 0) {
-    const int cnt = rs.npieces < kSlots ? rs.npieces : kSlots;
-    __syncthreads();  // every thread is done reading the ring
-    if (threadIdx.x == 0)
-      for (int j = 0; j < cnt; ++j) ring_issue<Tn>(sm, rs, rs.gbase, j, next_val, col);
-    rs.pre_count = cnt;
-    rs.pre_type = static_cast<int>(sizeof(Tn));
+__device__ __forceinline__ void stream_end_pass(const RingSmem& sm, WarpStream& ws, const Tn* next_val,
+                                                const int32_t* col) {
+  ws.gbase += static_cast<uint32_t>(ws.npieces);
+  ws.issued = ws.waited = ws.released = 0;
+  ws.pre_count = 0;
+  ws.pre_type = 0;
+  if (next_val != nullptr && ws.npieces > 0) {
+    const int cnt = ws.npieces < kSlots ? ws.npieces : kSlots;
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0)
+      for (int j = 0; j < cnt; ++j) stream_issue<Tn>(sm, ws, ws.gbase, j, next_val, col);
+    ws.pre_count = cnt;
+    ws.pre_type = static_cast<int>(sizeof(Tn));
   }
 }
 
 // Before leaving the kernel on an error path: wait (bounded) for the copies
-// this CTA still has in flight, so no bulk copy lands after the CTA is gone.
-__device__ __forceinline__ void ring_drain(const RingSmem& sm, RingState& rs, unsigned long long limit_ns) {
-  for (int j = rs.waited; j < rs.issued; ++j) ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns);
-  for (int j = 0; j < rs.pre_count; ++j) ring_wait_global(sm, rs.gbase + static_cast<uint32_t>(j), limit_ns);
+// this warp still has in flight.
+__device__ __forceinline__ void stream_drain(const RingSmem& sm, WarpStream& ws, unsigned long long limit_ns) {
+  for (int j = ws.waited; j < ws.issued; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
+  for (int j = 0; j < ws.pre_count; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
 }
 
 // Dot product of one row segment held in the ring: entries at ring positions
-// pos, pos+1, ... (masked), len of them, in storage order, with FMA.  Up to U
-// entries take a fully unrolled path that issues every gather before the
-// first multiply-add; longer segments go 8 at a time.
+// pos, pos+1, ... (masked), len of them, in storage order, with FMA.  Called
+// by all 32 lanes of the warp (len = 0 for lanes without a row).  Segments of
+// up to U entries take a fully unrolled path that issues every gather before
+// the first multiply-add, bounded by the warp's longest segment so that no
+// FP64 instruction is issued for a slot no lane needs (FP64 issue is the
+// scarce resource); longer segments go 8 at a time.
 template <typename T, typename X, typename Acc, int U>
 __device__ __forceinline__ Acc seg_dot(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
   Acc s = Acc(0);
-  // Called by all 32 lanes of the warp (len = 0 for lanes without a row).
-  // The unroll bound is the warp's longest segment, so no FP64 instruction is
-  // issued for a slot that no lane needs: FP64 issue is the scarce resource.
   const int wmax = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(len)));
   if (wmax <= U) {
-    // all gathers first (only they have long latency), then the FMAs with
-    // the values read from shared memory as they are consumed
     X xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -451,104 +446,109 @@ __device__ __forceinline__ Acc seg_dot(const T* rv, const int32_t* rc, int pos, 
   return s;
 }
 
-// Rows of chunk [r0, r1) from the ring; each result goes to epi(i, yi) from
-// the thread that holds it.  Entry k sits at ring position (k - kb + off) &
-// kRingMask.
-template <typename T, typename X, typename Acc, typename Epi>
-__device__ __forceinline__ void chunk_compute_ring(const RingSmem& sm, int mode, const int32_t* row_ptr, int r0,
-                                                   int r1, int kb, int off, const X* x, Epi& epi) {
-  const T* rv = sm.val<T>();
-  const int32_t* rc = sm.col();
-  if (mode == kThreadPerRow) {
-    const int i = r0 + static_cast<int>(threadIdx.x);
-    int ks = 0, len = 0;
-    if (i < r1) {
-      ks = row_ptr[i];
-      len = row_ptr[i + 1] - ks;
+// Lane-private part of a step: which entries this lane sums.
+struct LaneWork {
+  int row;   // row whose (partial) sum this lane computes, -1 if none
+  int ks;    // first entry
+  int len;   // number of entries
+};
+
+// Work of this lane in a lane-per-row or pair-per-row step (reads row_ptr).
+__device__ __forceinline__ LaneWork lane_work(const int32_t* row_ptr, int4 d, int mode) {
+  const int lane = threadIdx.x & 31;
+  LaneWork lw{-1, 0, 0};
+  if (mode == kLanePerRow) {
+    const int i = d.x + lane;
+    if (i < d.y) {
+      lw.row = i;
+      lw.ks = row_ptr[i];
+      lw.len = row_ptr[i + 1] - lw.ks;
     }
-    const Acc s = seg_dot<T, X, Acc, 16>(rv, rc, ks - kb + off, len, x);
-    if (i < r1) epi(i, s);
   } else if (mode == kPairPerRow) {
-    const int i = r0 + static_cast<int>(threadIdx.x >> 1);
-    const int h = threadIdx.x & 1;
-    int a = 0, len = 0;
-    if (i < r1) {
+    const int i = d.x + (lane >> 1);
+    if (i < d.y) {
       const int ks = row_ptr[i], ke = row_ptr[i + 1];
       const int half = (ke - ks + 1) >> 1;
-      a = h ? ks + half : ks;
-      len = h ? (ke - ks - half) : half;
-    }
-    const Acc part = seg_dot<T, X, Acc, 16>(rv, rc, a - kb + off, len, x);
-    // first half + second half: the same value in both lanes (commutative add)
-    const Acc other = __shfl_xor_sync(0xffffffffu, part, 1);
-    const Acc s = part + other;
-    if (h == 0 && i < r1) epi(i, s);
-  } else {  // kWarpPerRow
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = r0 + w; i < r1; i += kWarps) {
-      const int ks = row_ptr[i], ke = row_ptr[i + 1];
-      Acc acc = Acc(0);
-      for (int k = ks + lane; k < ke; k += 32) {
-        const int p = (k - kb + off) & kRingMask;
-        acc = fma(Acc(rv[p]), Acc(x[rc[p]]), acc);
-      }
-      if constexpr (sizeof(Acc) == 8) acc = warp_sum(acc);
-      else acc = warp_sum_f(acc);
-      if (lane == 0) epi(i, acc);
+      lw.row = i;
+      lw.ks = (lane & 1) ? ks + half : ks;
+      lw.len = (lane & 1) ? (ke - ks - half) : half;
     }
   }
+  return lw;
 }
 
-// One row longer than kChunkNnz, streamed from global memory by the whole CTA.
-template <typename T, typename X, typename Acc, typename Epi>
-__device__ __forceinline__ void chunk_compute_long(const int32_t* row_ptr, const int32_t* col_idx,
-                                                   const T* val, int i, const X* x, double* red, Epi& epi) {
-  const int ks = row_ptr[i], ke = row_ptr[i + 1];
-  Acc acc = Acc(0);
-  for (int k = ks + static_cast<int>(threadIdx.x); k < ke; k += kBlock)
-    acc = fma(Acc(val[k]), Acc(x[col_idx[k]]), acc);
-  const double tot = block_sum(static_cast<double>(acc), red);
-  if (threadIdx.x == 0) epi(i, static_cast<Acc>(tot));
-}
-
-// The product over the CTA's chunks [c0, c1) with values `val` of type T,
-// gathering x.  The pass starts from the pieces prefetched for it (if any)
-// and ends by prefetching the first pieces of the next pass (next_val, of
-// type Tn; nullptr for none).  Returns false if a wait gave up.
+// The product over this warp's steps with values `val` (type T), gathering x;
+// each row's result goes to epi(i, yi) from one lane.  The pass starts from
+// the pieces prefetched for it (if any) and ends by prefetching the first
+// pieces of the next pass (next_val of type Tn; nullptr for none).  Step
+// descriptors are loaded two steps ahead and the lanes' row pointers one step
+// ahead, so only the gathers' latency remains inside a step.  Returns false
+// (uniformly over the warp) if a wait gave up.
 template <typename T, typename X, typename Acc, typename Tn, typename Epi>
-__device__ __forceinline__ bool spmv_pass(const RingSmem& sm, RingState& rs, const DevCsr& A, const T* val,
-                                          int c0, int c1, const X* x, Epi& epi, const Tn* next_val,
-                                          unsigned long long limit_ns) {
+__device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, const DevCsr& A, const T* val,
+                                          const X* x, Epi& epi, const Tn* next_val, unsigned long long limit_ns) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* rv = sm.val<T>(w);
+  const int32_t* rc = sm.col(w);
   const int32_t* row_ptr = A.row_ptr;
-  const int32_t* cr = A.chunk_row;
-  const int32_t* cm = A.chunk_mode;
-  if (!ring_begin_pass<T>(sm, rs, val, A.col_idx, limit_ns)) return false;
-  const int off = ring_pos_of_piece0(rs.gbase);
-  for (int c = c0; c < c1; ++c) {
-    const int mode = cm[c];
-    const int r0 = cr[c], r1 = cr[c + 1];
-    const int k1 = row_ptr[r1];
-    if (mode == kBlockPerRow) {
-      chunk_compute_long<T, X, Acc>(row_ptr, A.col_idx, val, r0, x, sm.red(), epi);
+  if (!stream_begin_pass<T>(sm, ws, val, A.col_idx, limit_ns)) return false;
+  const int off = static_cast<int>((ws.gbase % kSlots) * kPiece) - ws.kb;  // ring pos = (k + off) & mask
+  Acc seg_acc = Acc(0);
+  int s = ws.s0;
+  int4 d = A.step[s];
+  int m = A.step_mode[s];
+  int4 dn = A.step[s + 1];       // sentinels follow the last step
+  int mn = A.step_mode[s + 1];
+  LaneWork lw = lane_work(row_ptr, d, m & 3);
+  for (; s < ws.s1; ++s) {
+    // prefetch: descriptor of step s+2, lane work of step s+1
+    const int4 dnn = A.step[s + 2];
+    const int mnn = A.step_mode[s + 2];
+    const LaneWork lwn = (s + 1 < ws.s1) ? lane_work(row_ptr, dn, mn & 3) : LaneWork{-1, 0, 0};
+    // the step's entries must be in the ring
+    if (d.w > d.z && !stream_wait_upto(sm, ws, ((d.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns)) return false;
+    const int mode = m & 3;
+    if (mode == kSegment) {
+      if (m & kSegFirst) seg_acc = Acc(0);
+      for (int k = d.z + lane; k < d.w; k += 32) {
+        const int p = (k + off) & kRingMask;
+        seg_acc = fma(Acc(rv[p]), Acc(x[rc[p]]), seg_acc);
+      }
+      if (m & kSegLast) {
+        Acc tot;
+        if constexpr (sizeof(Acc) == 8) tot = warp_sum(seg_acc);
+        else tot = warp_sum_f(seg_acc);
+        if (lane == 0) epi(d.x, tot);
+      }
     } else {
-      const int k0 = row_ptr[r0];
-      if (k1 > k0 && !ring_wait_upto(sm, rs, ((k1 - 1 - rs.kb) >> kPieceLog) + 1, limit_ns)) return false;
-      chunk_compute_ring<T, X, Acc>(sm, mode, row_ptr, r0, r1, rs.kb, off, x, epi);
+      const Acc part = seg_dot<T, X, Acc, 16>(rv, rc, lw.ks + off, lw.len, x);
+      if (mode == kPairPerRow) {
+        // first half + second half: the same value in both lanes (commutative add)
+        const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);
+        if ((lane & 1) == 0 && lw.row >= 0) epi(lw.row, sum);
+      } else if (lw.row >= 0) {
+        epi(lw.row, part);
+      }
     }
-    __syncthreads();  // the chunk's ring entries are consumed
-    // Release the pieces that end before the next chunk's first entry.  A slot
-    // is refilled only after its piece is complete, so pieces are waited for
-    // before release; a row longer than the ring (streamed from global memory)
-    // advances the ring in steps of at most kSlots pieces.
-    const int rel = (c + 1 == c1) ? rs.npieces : ((k1 - rs.kb) >> kPieceLog);
-    while (rel > rs.released) {
-      const int upto = rel < rs.issued ? rel : rs.issued;
-      if (!ring_wait_upto(sm, rs, upto, limit_ns)) return false;
-      rs.released = upto;
-      ring_fill<T>(sm, rs, val, A.col_idx);
+    // release the pieces that end before the next step's first entry and refill
+    const int next_e = (s + 1 < ws.s1) ? dn.z : ws.ke;
+    int rel = (s + 1 < ws.s1) ? ((next_e - ws.kb) >> kPieceLog) : ws.npieces;
+    if (rel > ws.released) {
+      __syncwarp();
+      while (rel > ws.released) {
+        const int upto = rel < ws.issued ? rel : ws.issued;
+        if (!stream_wait_upto(sm, ws, upto, limit_ns)) return false;  // a slot is refilled only once complete
+        ws.released = upto;
+        stream_fill<T>(sm, ws, val, A.col_idx);
+      }
     }
+    d = dn;
+    m = mn;
+    dn = dnn;
+    mn = mnn;
+    lw = lwn;
   }
-  ring_end_pass<Tn>(sm, rs, next_val, A.col_idx);
+  stream_end_pass<Tn>(sm, ws, next_val, A.col_idx);
   return true;
 }
 

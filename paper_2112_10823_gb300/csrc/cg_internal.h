@@ -6,50 +6,54 @@
 
 namespace cgk {
 
-// The persistent kernels run two 256-thread CTAs per SM: two independent
-// instruction streams whose memory-latency phases overlap each other's FP64
-// phases.
+// The persistent kernels run one 256-thread CTA per SM.
 constexpr int kBlock = 256;
-constexpr int kCtasPerSm = 2;
+constexpr int kCtasPerSm = 1;
 constexpr int kWarps = kBlock / 32;
 
-// Matrix stream of a CTA: its CSR values and column indices flow through a
-// shared-memory ring of kSlots pieces of kPiece entries, each piece one pair
-// of 1-D TMA bulk copies completing on the slot's mbarrier.
-constexpr int kPieceLog = 11;
-constexpr int kPiece = 1 << kPieceLog;  // 2048 entries
+// Matrix stream of a warp: each warp owns a contiguous run of rows and
+// streams their CSR values and column indices through a private
+// shared-memory ring of kSlots pieces of kPiece entries; a piece is one pair
+// of 1-D TMA bulk copies issued by the warp's lane 0 and completing on the
+// slot's mbarrier.  Warps never wait for each other inside the product.
+constexpr int kPieceLog = 9;
+constexpr int kPiece = 1 << kPieceLog;  // 512 entries
 constexpr int kSlots = 4;
-constexpr int kRing = kPiece * kSlots;  // 8192 entries: 64 KB of FP64 values + 32 KB of indices
+constexpr int kRing = kPiece * kSlots;  // 2048 entries per warp: 16 KB of FP64 values + 8 KB of indices
 constexpr int kRingMask = kRing - 1;
-// A compute chunk is a run of consecutive rows computed together: at most
-// kChunkNnz entries (half the ring, so the next pieces stream in meanwhile)
-// and at most kBlock rows (one thread per row) or kBlock/2 rows (two threads
-// per row).  A row longer than kChunkNnz is a chunk of its own, streamed from
-// global memory by the whole CTA.
-constexpr int kChunkNnz = kRing / 2;
+// A step is what a warp computes at once: up to 32 rows of <= 16 entries
+// (one lane per row), up to 16 rows of <= 64 entries (two lanes per row), or
+// a segment of <= kSegNnz entries of one longer row (lanes stride the
+// segment; the row's sum is completed at its last segment).  A step holds at
+// most kStepNnz entries (half the ring, so later pieces stream in meanwhile).
+constexpr int kStepNnz = kRing / 2;
+constexpr int kSegNnz = kPiece;
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
 constexpr int kPadEntries = 8;
 
-enum ChunkMode : int32_t {
-  kThreadPerRow = 0,  // rows of <= 16 entries: thread t computes row r0 + t
-  kPairPerRow = 1,    // rows of <= 64 entries: threads 2t, 2t+1 split row r0 + t
-  kWarpPerRow = 2,    // longer rows: warp w computes rows r0 + w, r0 + w + 8, ...
-  kBlockPerRow = 3,   // one row longer than kChunkNnz, streamed from global memory
+enum StepMode : int32_t {
+  kLanePerRow = 0,   // lane l computes row r0 + l
+  kPairPerRow = 1,   // lanes 2t, 2t+1 split row r0 + t
+  kSegment = 2,      // entries [e0, e1) of row r0; lanes stride them
 };
+// Flags of a kSegment step (stored above the mode bits).
+constexpr int32_t kSegFirst = 4;
+constexpr int32_t kSegLast = 8;
 
-// Device view of a CSR matrix with its chunk partition.
+// Device view of a CSR matrix with its step partition.
 struct DevCsr {
   const int32_t* row_ptr;     // [n+1], 0-based
   const int32_t* col_idx;     // [nnz + kPadEntries]
   const double* val;          // [nnz + kPadEntries]
   const float* val32;         // [nnz + kPadEntries] FP32 copy (mixed precision) or nullptr
-  const int32_t* chunk_row;   // [nchunks+1] first row of each chunk
-  const int32_t* chunk_mode;  // [nchunks]
-  const int32_t* block_chunk; // [nblocks+1] first chunk of each persistent CTA
+  const int4* step;           // [nsteps + 2] {r0, r1, e0, e1} (two trailing sentinels)
+  const int32_t* step_mode;   // [nsteps + 2] StepMode | flags
+  const int32_t* warp_step;   // [nblocks * kWarps + 1] first step of each warp
+  const int32_t* block_row;   // [nblocks + 1] first row of each CTA (vector phases)
   int32_t n;
-  int32_t nchunks;
-  int32_t nblocks;            // CTAs the chunk partition was balanced for
+  int32_t nsteps;
+  int32_t nblocks;            // CTAs the partition was balanced for
   int64_t nnz;
 };
 

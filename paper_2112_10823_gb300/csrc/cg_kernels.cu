@@ -27,8 +27,8 @@
 namespace cgk {
 
 // Leave the kernel after a failed wait: drain in-flight copies, record status.
-__device__ __forceinline__ void solve_fail(const RingSmem& sm, RingState& rs, const SolveParams& P) {
-  ring_drain(sm, rs, P.wait_limit_ns);
+__device__ __forceinline__ void solve_fail(const RingSmem& sm, WarpStream& rs, const SolveParams& P) {
+  stream_drain(sm, rs, P.wait_limit_ns);
   if (threadIdx.x == 0) {
     atomicExch(&P.ctrl->abort, 1);
     atomicExch(&P.ctrl->status, kETIMEOUT);
@@ -45,8 +45,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   const DevCsr& A = P.A;
   const int bid = blockIdx.x;
   const int tid = threadIdx.x;
-  const int c0 = A.block_chunk[bid], c1 = A.block_chunk[bid + 1];
-  const int row0 = A.chunk_row[c0], row1 = A.chunk_row[c1];
+  const int row0 = A.block_row[bid], row1 = A.block_row[bid + 1];
   const unsigned long long lim = P.wait_limit_ns;
   int32_t* flag = sm.flag();
   double* sc = sm.scalars();  // broadcast slots for per-step scalars
@@ -63,8 +62,8 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   const float* const no_next32 = nullptr;
   (void)no_next32;
 
-  RingState rs;
-  ring_init(sm, rs, A, row0, row1);
+  WarpStream rs;
+  stream_init(sm, rs, A);
   GridBarrier gb;
   int slot = 0;
   int site = 0;
@@ -105,14 +104,14 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       acc_bb = fma(bi, bi, acc_bb);
     };
     bool ok;
-    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val32, lim);
-    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val, lim);
+    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val32, lim);
+    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val, lim);
     if (!ok) { solve_fail(sm, rs, P); return; }
   }
   double rho, bnorm2;
   if (!allreduce(acc_rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, rs, P); return; }
   if (bnorm2 == 0.0) {  // b = 0: the solution is 0
-    ring_drain(sm, rs, lim);
+    stream_drain(sm, rs, lim);
     for (int i = row0 + tid; i < row1; i += kBlock) x[i] = 0.0;
     if (bid == 0 && tid == 0) {
       ctrl->status = kOK;
@@ -141,13 +140,13 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
         q[i] = qi;
         acc_g = fma(p[i], qi, acc_g);
       };
-      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, c0, c1, p32, epi, A.val32, lim);
+      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, p32, epi, A.val32, lim);
     } else {
       auto epi = [&](int i, double s) {
         q[i] = s;
         acc_g = fma(p[i], s, acc_g);
       };
-      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, p, epi, A.val, lim);
+      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, p, epi, A.val, lim);
     }
     double gamma;
     if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, rs, P); return; }
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
       };
-      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, A.val32, lim) ||
+      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val32, lim) ||
           !allreduce(acc_t, rho_new)) {
         solve_fail(sm, rs, P);
         return;
@@ -258,7 +257,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       acc_t = fma(d, d, acc_t);
     };
     double tsum;
-    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, no_next, lim) ||
+    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, no_next, lim) ||
         !allreduce(acc_t, tsum)) {
       solve_fail(sm, rs, P);
       return;
@@ -275,19 +274,18 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   }
 }
 
-// y = A x over the CTA's chunk range (same partition and stream as the solve).
+// y = A x over the CTA's rows (same partition and streams as the solve).
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A, const double* __restrict__ x,
-                                                          double* __restrict__ y, int32_t* err) {
+                                                                   double* __restrict__ y, int32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
-  const int c0 = A.block_chunk[blockIdx.x], c1 = A.block_chunk[blockIdx.x + 1];
-  RingState rs;
-  ring_init(sm, rs, A, A.chunk_row[c0], A.chunk_row[c1]);
+  WarpStream ws;
+  stream_init(sm, ws, A);
   auto epi = [&](int i, double s) { y[i] = s; };
   const double* const no_next = nullptr;
-  if (!spmv_pass<double, double, double>(sm, rs, A, A.val, c0, c1, x, epi, no_next, 2000000000ull)) {
-    ring_drain(sm, rs, 2000000000ull);
-    if (threadIdx.x == 0) atomicExch(err, kETIMEOUT);
+  if (!spmv_pass<double, double, double>(sm, ws, A, A.val, x, epi, no_next, 2000000000ull)) {
+    stream_drain(sm, ws, 2000000000ull);
+    if ((threadIdx.x & 31) == 0) atomicExch(err, kETIMEOUT);
   }
 }
 
