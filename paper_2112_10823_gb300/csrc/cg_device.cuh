@@ -410,27 +410,32 @@ __device__ __forceinline__ void stream_drain(const RingSmem& sm, WarpStream& ws,
   for (int j = 0; j < ws.pre_count; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
 }
 
-// Dot product of one row segment held in the ring: entries at ring positions
-// pos, pos+1, ... (masked), len of them, in storage order, with FMA.  Called
-// by all 32 lanes of the warp (len = 0 for lanes without a row).  Segments of
-// up to U entries take a fully unrolled path that issues every gather before
-// the first multiply-add, bounded by the warp's longest segment so that no
-// FP64 instruction is issued for a slot no lane needs (FP64 issue is the
-// scarce resource); longer segments go 8 at a time.
+// Gathers of one lane's row segment: xv[u] = x[col of entry u] for the len
+// entries at ring positions pos, pos+1, ... (masked).  Called by all 32 lanes
+// (len = 0 for lanes without a row); wmax is the warp's longest segment, so no
+// instruction is issued for a slot no lane needs.
+template <typename X, int U>
+__device__ __forceinline__ void seg_gather(const int32_t* rc, int pos, int len, int wmax, const X* x, X (&xv)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (u < wmax && u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
+}
+
+// Multiply-adds of a gathered segment, in storage order, with FMA.
 template <typename T, typename X, typename Acc, int U>
-__device__ __forceinline__ Acc seg_dot(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
+__device__ __forceinline__ Acc seg_fma(const T* rv, int pos, int len, int wmax, const X (&xv)[U]) {
   Acc s = Acc(0);
-  const int wmax = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(len)));
-  if (wmax <= U) {
-    X xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (u < wmax && u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (u < wmax && u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
-    return s;
-  }
+  for (int u = 0; u < U; ++u)
+    if (u < wmax && u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
+  return s;
+}
+
+// A segment longer than the unrolled capacity: gathers and multiply-adds 8 at
+// a time (rows of 17..64 entries split over two lanes can reach 32 per lane).
+template <typename T, typename X, typename Acc>
+__device__ __forceinline__ Acc seg_dot_loop(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
+  Acc s = Acc(0);
   int t = 0;
   for (; t + 8 <= len; t += 8) {
     X xv[8];
@@ -451,20 +456,22 @@ struct LaneWork {
   int row;   // row whose (partial) sum this lane computes, -1 if none
   int ks;    // first entry
   int len;   // number of entries
+  int wmax;  // longest segment in the warp (uniform)
 };
 
 // Work of this lane in a lane-per-row or pair-per-row step (reads row_ptr).
-__device__ __forceinline__ LaneWork lane_work(const int32_t* row_ptr, int4 d, int mode) {
+// All 32 lanes call it.
+__device__ __forceinline__ LaneWork lane_work(const int32_t* row_ptr, int4 d, int mode, bool valid) {
   const int lane = threadIdx.x & 31;
-  LaneWork lw{-1, 0, 0};
-  if (mode == kLanePerRow) {
+  LaneWork lw{-1, 0, 0, 0};
+  if (valid && mode == kLanePerRow) {
     const int i = d.x + lane;
     if (i < d.y) {
       lw.row = i;
       lw.ks = row_ptr[i];
       lw.len = row_ptr[i + 1] - lw.ks;
     }
-  } else if (mode == kPairPerRow) {
+  } else if (valid && mode == kPairPerRow) {
     const int i = d.x + (lane >> 1);
     if (i < d.y) {
       const int ks = row_ptr[i], ke = row_ptr[i + 1];
@@ -474,16 +481,20 @@ __device__ __forceinline__ LaneWork lane_work(const int32_t* row_ptr, int4 d, in
       lw.len = (lane & 1) ? (ke - ks - half) : half;
     }
   }
+  lw.wmax = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(lw.len)));
   return lw;
 }
 
+constexpr int kUnroll = 16;  // entries per lane gathered at once
+
 // The product over this warp's steps with values `val` (type T), gathering x;
-// each row's result goes to epi(i, yi) from one lane.  The pass starts from
+// each row's result goes to epi(i, yi) from one lane.  Software-pipelined:
+// the gathers of step s+1 are issued before the multiply-adds of step s, so
+// the gathers' latency hides behind FP64 work; step descriptors are loaded
+// three steps ahead and row pointers two steps ahead.  The pass starts from
 // the pieces prefetched for it (if any) and ends by prefetching the first
-// pieces of the next pass (next_val of type Tn; nullptr for none).  Step
-// descriptors are loaded two steps ahead and the lanes' row pointers one step
-// ahead, so only the gathers' latency remains inside a step.  Returns false
-// (uniformly over the warp) if a wait gave up.
+// pieces of the next pass (next_val of type Tn; nullptr for none).  Returns
+// false (uniformly over the warp) if a wait gave up.
 template <typename T, typename X, typename Acc, typename Tn, typename Epi>
 __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, const DevCsr& A, const T* val,
                                           const X* x, Epi& epi, const Tn* next_val, unsigned long long limit_ns) {
@@ -493,46 +504,61 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
   const int32_t* row_ptr = A.row_ptr;
   if (!stream_begin_pass<T>(sm, ws, val, A.col_idx, limit_ns)) return false;
   const int off = static_cast<int>((ws.gbase % kSlots) * kPiece) - ws.kb;  // ring pos = (k + off) & mask
+  auto wait_step = [&](int4 dd) -> bool {
+    return dd.w <= dd.z || stream_wait_upto(sm, ws, ((dd.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns);
+  };
   Acc seg_acc = Acc(0);
   int s = ws.s0;
-  int4 d = A.step[s];
-  int m = A.step_mode[s];
-  int4 dn = A.step[s + 1];       // sentinels follow the last step
-  int mn = A.step_mode[s + 1];
-  LaneWork lw = lane_work(row_ptr, d, m & 3);
+  // descriptor index clamped to the array (two sentinels follow the last step)
+  auto sd = [&](int k) { return k < A.nsteps + 2 ? k : A.nsteps + 1; };
+  int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + 1)], d2 = A.step[sd(s + 2)];
+  int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + 1)], m2 = A.step_mode[sd(s + 2)];
+  LaneWork lw0 = lane_work(row_ptr, d0, m0 & 3, s < ws.s1);
+  LaneWork lw1 = lane_work(row_ptr, d1, m1 & 3, s + 1 < ws.s1);
+  X xc[kUnroll];  // gathered x of step s
+  if (s < ws.s1) {
+    if (!wait_step(d0)) return false;
+    if ((m0 & 3) != kSegment && lw0.wmax <= kUnroll) seg_gather<X, kUnroll>(rc, lw0.ks + off, lw0.len, lw0.wmax, x, xc);
+  }
   for (; s < ws.s1; ++s) {
-    // prefetch: descriptor of step s+2, lane work of step s+1
-    const int4 dnn = A.step[s + 2];
-    const int mnn = A.step_mode[s + 2];
-    const LaneWork lwn = (s + 1 < ws.s1) ? lane_work(row_ptr, dn, mn & 3) : LaneWork{-1, 0, 0};
-    // the step's entries must be in the ring
-    if (d.w > d.z && !stream_wait_upto(sm, ws, ((d.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns)) return false;
-    const int mode = m & 3;
+    const bool has1 = s + 1 < ws.s1;
+    // prefetch: descriptor of step s+3, row pointers of step s+2
+    const int4 d3 = A.step[sd(s + 3)];
+    const int m3 = A.step_mode[sd(s + 3)];
+    const LaneWork lw2 = lane_work(row_ptr, d2, m2 & 3, s + 2 < ws.s1);
+    // gathers of step s+1 (its entries must be in the ring)
+    X xn[kUnroll];
+    if (has1) {
+      if (!wait_step(d1)) return false;
+      if ((m1 & 3) != kSegment && lw1.wmax <= kUnroll) seg_gather<X, kUnroll>(rc, lw1.ks + off, lw1.len, lw1.wmax, x, xn);
+    }
+    // multiply-adds of step s
+    const int mode = m0 & 3;
     if (mode == kSegment) {
-      if (m & kSegFirst) seg_acc = Acc(0);
-      for (int k = d.z + lane; k < d.w; k += 32) {
+      if (m0 & kSegFirst) seg_acc = Acc(0);
+      for (int k = d0.z + lane; k < d0.w; k += 32) {
         const int p = (k + off) & kRingMask;
         seg_acc = fma(Acc(rv[p]), Acc(x[rc[p]]), seg_acc);
       }
-      if (m & kSegLast) {
+      if (m0 & kSegLast) {
         Acc tot;
         if constexpr (sizeof(Acc) == 8) tot = warp_sum(seg_acc);
         else tot = warp_sum_f(seg_acc);
-        if (lane == 0) epi(d.x, tot);
+        if (lane == 0) epi(d0.x, tot);
       }
     } else {
-      const Acc part = seg_dot<T, X, Acc, 16>(rv, rc, lw.ks + off, lw.len, x);
+      const Acc part = lw0.wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv, lw0.ks + off, lw0.len, lw0.wmax, xc)
+                                           : seg_dot_loop<T, X, Acc>(rv, rc, lw0.ks + off, lw0.len, x);
       if (mode == kPairPerRow) {
         // first half + second half: the same value in both lanes (commutative add)
         const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);
-        if ((lane & 1) == 0 && lw.row >= 0) epi(lw.row, sum);
-      } else if (lw.row >= 0) {
-        epi(lw.row, part);
+        if ((lane & 1) == 0 && lw0.row >= 0) epi(lw0.row, sum);
+      } else if (lw0.row >= 0) {
+        epi(lw0.row, part);
       }
     }
-    // release the pieces that end before the next step's first entry and refill
-    const int next_e = (s + 1 < ws.s1) ? dn.z : ws.ke;
-    int rel = (s + 1 < ws.s1) ? ((next_e - ws.kb) >> kPieceLog) : ws.npieces;
+    // release the pieces that end before step s+1's first entry and refill
+    const int rel = has1 ? ((d1.z - ws.kb) >> kPieceLog) : ws.npieces;
     if (rel > ws.released) {
       __syncwarp();
       while (rel > ws.released) {
@@ -542,11 +568,11 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         stream_fill<T>(sm, ws, val, A.col_idx);
       }
     }
-    d = dn;
-    m = mn;
-    dn = dnn;
-    mn = mnn;
-    lw = lwn;
+    d0 = d1; m0 = m1; lw0 = lw1;
+    d1 = d2; m1 = m2; lw1 = lw2;
+    d2 = d3; m2 = m3;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) xc[u] = xn[u];
   }
   stream_end_pass<Tn>(sm, ws, next_val, A.col_idx);
   return true;

@@ -25,8 +25,10 @@ constexpr int kRingMask = kRing - 1;
 // (one lane per row), up to 16 rows of <= 64 entries (two lanes per row), or
 // a segment of <= kSegNnz entries of one longer row (lanes stride the
 // segment; the row's sum is completed at its last segment).  A step holds at
-// most kStepNnz entries (half the ring, so later pieces stream in meanwhile).
-constexpr int kStepNnz = kRing / 2;
+// most kStepNnz entries: a quarter of the ring, so that two consecutive steps
+// (the one being multiplied and the next, whose gathers are already in
+// flight) stay resident while later pieces stream in.
+constexpr int kStepNnz = kRing / 4;
 constexpr int kSegNnz = kPiece;
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
