@@ -251,10 +251,12 @@ struct GridBarrier {
 
 // Shared memory of a CTA: one ring per warp (values sized for FP64, the FP32
 // product uses the first half of a warp's value ring), the column-index
-// rings, kSlots mbarriers per warp, reduction scratch and broadcast words.
+// rings, each followed by its kMirror-entry mirror, kSlots mbarriers per warp,
+// reduction scratch and broadcast words.
 struct RingSmem {
-  static constexpr size_t kValBytes = sizeof(double) * kRing * kWarps;
-  static constexpr size_t kColBytes = sizeof(int32_t) * kRing * kWarps;
+  static constexpr int kRingAlloc = kRing + kMirror;
+  static constexpr size_t kValBytes = sizeof(double) * kRingAlloc * kWarps;
+  static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc * kWarps;
   static constexpr size_t kBarOff = kValBytes + kColBytes;
   static constexpr size_t kRedOff = kBarOff + 8 * kSlots * kWarps;
   static constexpr size_t kRedBytes = sizeof(double) * (kBlock + 8);
@@ -265,8 +267,8 @@ struct RingSmem {
 
   unsigned char* base;
   template <typename T>
-  __device__ T* val(int w) const { return reinterpret_cast<T*>(base + sizeof(double) * kRing * w); }
-  __device__ int32_t* col(int w) const { return reinterpret_cast<int32_t*>(base + kValBytes) + kRing * w; }
+  __device__ T* val(int w) const { return reinterpret_cast<T*>(base + sizeof(double) * kRingAlloc * w); }
+  __device__ int32_t* col(int w) const { return reinterpret_cast<int32_t*>(base + kValBytes) + kRingAlloc * w; }
   __device__ uint64_t* bar(int w, int s) const {
     return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots * w + s;
   }
@@ -321,10 +323,17 @@ __device__ __forceinline__ void stream_issue(const RingSmem& sm, const WarpStrea
   const int pos = slot * kPiece;
   const uint32_t bv = static_cast<uint32_t>(e1 - e0) * sizeof(T);
   const uint32_t bc = static_cast<uint32_t>(e1 - e0) * 4u;
+  // slot 0 also fills the mirror behind the ring end with its first entries
+  const int nm = slot == 0 ? (e1 - e0 < kMirror ? e1 - e0 : kMirror) : 0;  // a multiple of 4
+  const uint32_t mv = static_cast<uint32_t>(nm) * sizeof(T), mc = static_cast<uint32_t>(nm) * 4u;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(sm.bar(w, slot), bv + bc);
+  mbar_arrive_expect_tx(sm.bar(w, slot), bv + bc + mv + mc);
   bulk_g2s(sm.val<T>(w) + pos, val + e0, bv, sm.bar(w, slot));
   bulk_g2s(sm.col(w) + pos, col + e0, bc, sm.bar(w, slot));
+  if (nm) {
+    bulk_g2s(sm.val<T>(w) + kRing, val + e0, mv, sm.bar(w, slot));
+    bulk_g2s(sm.col(w) + kRing, col + e0, mc, sm.bar(w, slot));
+  }
 }
 
 // Wait (bounded) for global piece g of this warp; uniform over the warp.
@@ -410,44 +419,43 @@ __device__ __forceinline__ void stream_drain(const RingSmem& sm, WarpStream& ws,
   for (int j = 0; j < ws.pre_count; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
 }
 
-// Gathers of one lane's row segment: xv[u] = x[col of entry u] for the len
-// entries at ring positions pos, pos+1, ... (masked).  Called by all 32 lanes
-// (len = 0 for lanes without a row); wmax is the warp's longest segment, so no
-// instruction is issued for a slot no lane needs.
+// Gathers of one lane's row segment: xv[u] = x[cp[u]] for its len entries,
+// cp pointing at the segment's column indices in the ring (contiguous thanks
+// to the mirror).  Called by all 32 lanes (len = 0 for lanes without a row);
+// wmax is the warp's longest segment, so no instruction is issued for a slot
+// no lane needs.
 template <typename X, int U>
-__device__ __forceinline__ void seg_gather(const int32_t* rc, int pos, int len, int wmax, const X* x, X (&xv)[U]) {
+__device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
 #pragma unroll
   for (int u = 0; u < U; ++u)
-    if (u < wmax && u < len) xv[u] = x[rc[(pos + u) & kRingMask]];
+    if (u < wmax && u < len) xv[u] = x[cp[u]];
 }
 
 // Multiply-adds of a gathered segment, in storage order, with FMA.
 template <typename T, typename X, typename Acc, int U>
-__device__ __forceinline__ Acc seg_fma(const T* rv, int pos, int len, int wmax, const X (&xv)[U]) {
+__device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U]) {
   Acc s = Acc(0);
 #pragma unroll
   for (int u = 0; u < U; ++u)
-    if (u < wmax && u < len) s = fma(Acc(rv[(pos + u) & kRingMask]), Acc(xv[u]), s);
+    if (u < wmax && u < len) s = fma(Acc(vp[u]), Acc(xv[u]), s);
   return s;
 }
 
-// A segment longer than the unrolled capacity: gathers and multiply-adds 8 at
-// a time (rows of 17..64 entries split over two lanes can reach 32 per lane).
+// A segment longer than the unrolled capacity (up to kMirror entries: rows of
+// 17..64 entries split over two lanes), contiguous in the ring: gathers and
+// multiply-adds 8 at a time.
 template <typename T, typename X, typename Acc>
-__device__ __forceinline__ Acc seg_dot_loop(const T* rv, const int32_t* rc, int pos, int len, const X* x) {
+__device__ __forceinline__ Acc seg_dot_loop(const T* vp, const int32_t* cp, int len, const X* x) {
   Acc s = Acc(0);
   int t = 0;
   for (; t + 8 <= len; t += 8) {
     X xv[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = x[rc[(pos + t + u) & kRingMask]];
+    for (int u = 0; u < 8; ++u) xv[u] = x[cp[t + u]];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s = fma(Acc(rv[(pos + t + u) & kRingMask]), Acc(xv[u]), s);
+    for (int u = 0; u < 8; ++u) s = fma(Acc(vp[t + u]), Acc(xv[u]), s);
   }
-  for (; t < len; ++t) {
-    const int p = (pos + t) & kRingMask;
-    s = fma(Acc(rv[p]), Acc(x[rc[p]]), s);
-  }
+  for (; t < len; ++t) s = fma(Acc(vp[t]), Acc(x[cp[t]]), s);
   return s;
 }
 
@@ -516,9 +524,11 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
   LaneWork lw0 = lane_work(row_ptr, d0, m0 & 3, s < ws.s1);
   LaneWork lw1 = lane_work(row_ptr, d1, m1 & 3, s + 1 < ws.s1);
   X xc[kUnroll];  // gathered x of step s
+  // ring position of a lane's first entry (its segment then reads contiguously)
+  auto rpos = [&](const LaneWork& l) { return (l.ks + off) & kRingMask; };
   if (s < ws.s1) {
     if (!wait_step(d0)) return false;
-    if ((m0 & 3) != kSegment && lw0.wmax <= kUnroll) seg_gather<X, kUnroll>(rc, lw0.ks + off, lw0.len, lw0.wmax, x, xc);
+    if ((m0 & 3) != kSegment && lw0.wmax <= kUnroll) seg_gather<X, kUnroll>(rc + rpos(lw0), lw0.len, lw0.wmax, x, xc);
   }
   for (; s < ws.s1; ++s) {
     const bool has1 = s + 1 < ws.s1;
@@ -530,7 +540,7 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
     X xn[kUnroll];
     if (has1) {
       if (!wait_step(d1)) return false;
-      if ((m1 & 3) != kSegment && lw1.wmax <= kUnroll) seg_gather<X, kUnroll>(rc, lw1.ks + off, lw1.len, lw1.wmax, x, xn);
+      if ((m1 & 3) != kSegment && lw1.wmax <= kUnroll) seg_gather<X, kUnroll>(rc + rpos(lw1), lw1.len, lw1.wmax, x, xn);
     }
     // multiply-adds of step s
     const int mode = m0 & 3;
@@ -547,8 +557,9 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         if (lane == 0) epi(d0.x, tot);
       }
     } else {
-      const Acc part = lw0.wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv, lw0.ks + off, lw0.len, lw0.wmax, xc)
-                                           : seg_dot_loop<T, X, Acc>(rv, rc, lw0.ks + off, lw0.len, x);
+      const int p0 = rpos(lw0);
+      const Acc part = lw0.wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv + p0, lw0.len, lw0.wmax, xc)
+                                           : seg_dot_loop<T, X, Acc>(rv + p0, rc + p0, lw0.len, x);
       if (mode == kPairPerRow) {
         // first half + second half: the same value in both lanes (commutative add)
         const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);

@@ -21,6 +21,10 @@ constexpr int kPiece = 1 << kPieceLog;  // 512 entries
 constexpr int kSlots = 4;
 constexpr int kRing = kPiece * kSlots;  // 2048 entries per warp: 16 KB of FP64 values + 8 KB of indices
 constexpr int kRingMask = kRing - 1;
+// Entries mirrored behind the end of each ring: the head of the piece in
+// slot 0 is copied there as well, so a row segment of up to kMirror entries
+// starting anywhere in the ring reads contiguously, without wrapping.
+constexpr int kMirror = 32;
 // A step is what a warp computes at once: up to 32 rows of <= 16 entries
 // (one lane per row), up to 16 rows of <= 64 entries (two lanes per row), or
 // a segment of <= kSegNnz entries of one longer row (lanes stride the
