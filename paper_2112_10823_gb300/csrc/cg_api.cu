@@ -158,7 +158,10 @@ void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partit
       ++row;
     }
     P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
-    P.step_mode.push_back(maxlen <= 16 ? cgk::kLanePerRow : cgk::kPairPerRow);
+    const bool lane_mode = maxlen <= 16;
+    const int64_t wmax = lane_mode ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
+    P.step_mode.push_back((lane_mode ? cgk::kLanePerRow : cgk::kPairPerRow) |
+                          static_cast<int32_t>(wmax << cgk::kWmaxShift));
   }
 }
 

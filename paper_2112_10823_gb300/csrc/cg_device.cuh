@@ -459,53 +459,60 @@ __device__ __forceinline__ Acc seg_dot_loop(const T* vp, const int32_t* cp, int 
   return s;
 }
 
-// Lane-private part of a step: which entries this lane sums.
-struct LaneWork {
+// Lane-private part of a lane-per-row or pair-per-row step.  The row
+// pointers are loaded when a step is two steps ahead and only consumed one
+// step later, so their latency stays off the critical path.
+struct LaneRaw {
   int row;   // row whose (partial) sum this lane computes, -1 if none
-  int ks;    // first entry
-  int len;   // number of entries
-  int wmax;  // longest segment in the warp (uniform)
+  int ks;    // row_ptr[row]
+  int ke;    // row_ptr[row + 1]
 };
 
-// Work of this lane in a lane-per-row or pair-per-row step (reads row_ptr).
-// All 32 lanes call it.
-__device__ __forceinline__ LaneWork lane_work(const int32_t* row_ptr, int4 d, int mode, bool valid) {
+__device__ __forceinline__ LaneRaw lane_raw(const int32_t* row_ptr, int4 d, int mode, bool valid) {
   const int lane = threadIdx.x & 31;
-  LaneWork lw{-1, 0, 0, 0};
-  if (valid && mode == kLanePerRow) {
-    const int i = d.x + lane;
+  LaneRaw r{-1, 0, 0};
+  if (valid && mode != kSegment) {
+    const int i = d.x + (mode == kLanePerRow ? lane : (lane >> 1));
     if (i < d.y) {
-      lw.row = i;
-      lw.ks = row_ptr[i];
-      lw.len = row_ptr[i + 1] - lw.ks;
-    }
-  } else if (valid && mode == kPairPerRow) {
-    const int i = d.x + (lane >> 1);
-    if (i < d.y) {
-      const int ks = row_ptr[i], ke = row_ptr[i + 1];
-      const int half = (ke - ks + 1) >> 1;
-      lw.row = i;
-      lw.ks = (lane & 1) ? ks + half : ks;
-      lw.len = (lane & 1) ? (ke - ks - half) : half;
+      r.row = i;
+      r.ks = row_ptr[i];
+      r.ke = row_ptr[i + 1];
     }
   }
-  lw.wmax = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(lw.len)));
-  return lw;
+  return r;
+}
+
+// This lane's entries [a, a + len) of its row (half of it in a pair step).
+__device__ __forceinline__ void lane_span(const LaneRaw& r, int mode, int& a, int& len) {
+  if (r.row < 0) {
+    a = 0;
+    len = 0;
+  } else if (mode == kLanePerRow) {
+    a = r.ks;
+    len = r.ke - r.ks;
+  } else {
+    const int half = (r.ke - r.ks + 1) >> 1;
+    const bool second = threadIdx.x & 1;
+    a = second ? r.ks + half : r.ks;
+    len = second ? (r.ke - r.ks - half) : half;
+  }
 }
 
 constexpr int kUnroll = 16;  // entries per lane gathered at once
 
 // The product over this warp's steps with values `val` (type T), gathering x;
-// each row's result goes to epi(i, yi) from one lane.  Software-pipelined:
-// the gathers of step s+1 are issued before the multiply-adds of step s, so
-// the gathers' latency hides behind FP64 work; step descriptors are loaded
-// three steps ahead and row pointers two steps ahead.  The pass starts from
-// the pieces prefetched for it (if any) and ends by prefetching the first
-// pieces of the next pass (next_val of type Tn; nullptr for none).  Returns
-// false (uniformly over the warp) if a wait gave up.
+// each row's result goes to epi(i, yi, aux[i]) from one lane (aux[i] = 0 when
+// aux is nullptr).  Software-pipelined: the gathers of step s+1 and its aux
+// values are issued before the multiply-adds of step s, the row pointers two
+// steps ahead and the descriptors three steps ahead, so within a step only
+// FP64 work and shared-memory reads remain.  The pass starts from the pieces
+// prefetched for it (if any) and ends by prefetching the first pieces of the
+// next pass (next_val of type Tn; nullptr for none).  Returns false
+// (uniformly over the warp) if a wait gave up.
 template <typename T, typename X, typename Acc, typename Tn, typename Epi>
 __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, const DevCsr& A, const T* val,
-                                          const X* x, Epi& epi, const Tn* next_val, unsigned long long limit_ns) {
+                                          const X* x, const double* aux, Epi& epi, const Tn* next_val,
+                                          unsigned long long limit_ns) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* rv = sm.val<T>(w);
   const int32_t* rc = sm.col(w);
@@ -515,32 +522,43 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
   auto wait_step = [&](int4 dd) -> bool {
     return dd.w <= dd.z || stream_wait_upto(sm, ws, ((dd.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns);
   };
-  Acc seg_acc = Acc(0);
-  int s = ws.s0;
   // descriptor index clamped to the array (two sentinels follow the last step)
   auto sd = [&](int k) { return k < A.nsteps + 2 ? k : A.nsteps + 1; };
+  auto holds_result = [&](int mode, const LaneRaw& r) {
+    return r.row >= 0 && (mode == kLanePerRow || (lane & 1) == 0);
+  };
+  Acc seg_acc = Acc(0);
+  int s = ws.s0;
   int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + 1)], d2 = A.step[sd(s + 2)];
   int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + 1)], m2 = A.step_mode[sd(s + 2)];
-  LaneWork lw0 = lane_work(row_ptr, d0, m0 & 3, s < ws.s1);
-  LaneWork lw1 = lane_work(row_ptr, d1, m1 & 3, s + 1 < ws.s1);
-  X xc[kUnroll];  // gathered x of step s
-  // ring position of a lane's first entry (its segment then reads contiguously)
-  auto rpos = [&](const LaneWork& l) { return (l.ks + off) & kRingMask; };
+  LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < ws.s1);
+  LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, s + 1 < ws.s1);
+  X xc[kUnroll];      // gathered x of step s
+  double ac = 0.0;    // aux value of this lane's row in step s
   if (s < ws.s1) {
     if (!wait_step(d0)) return false;
-    if ((m0 & 3) != kSegment && lw0.wmax <= kUnroll) seg_gather<X, kUnroll>(rc + rpos(lw0), lw0.len, lw0.wmax, x, xc);
+    const int mode = m0 & 3, wmax = (m0 >> kWmaxShift) & 0xff;
+    int a, len;
+    lane_span(r0, mode, a, len);
+    if (mode != kSegment && wmax <= kUnroll) seg_gather<X, kUnroll>(rc + ((a + off) & kRingMask), len, wmax, x, xc);
+    if (aux != nullptr && holds_result(mode, r0)) ac = aux[r0.row];
   }
   for (; s < ws.s1; ++s) {
     const bool has1 = s + 1 < ws.s1;
     // prefetch: descriptor of step s+3, row pointers of step s+2
     const int4 d3 = A.step[sd(s + 3)];
     const int m3 = A.step_mode[sd(s + 3)];
-    const LaneWork lw2 = lane_work(row_ptr, d2, m2 & 3, s + 2 < ws.s1);
-    // gathers of step s+1 (its entries must be in the ring)
+    const LaneRaw r2 = lane_raw(row_ptr, d2, m2 & 3, s + 2 < ws.s1);
+    // gathers and aux values of step s+1 (its entries must be in the ring)
     X xn[kUnroll];
+    double an = 0.0;
     if (has1) {
       if (!wait_step(d1)) return false;
-      if ((m1 & 3) != kSegment && lw1.wmax <= kUnroll) seg_gather<X, kUnroll>(rc + rpos(lw1), lw1.len, lw1.wmax, x, xn);
+      const int mode = m1 & 3, wmax = (m1 >> kWmaxShift) & 0xff;
+      int a, len;
+      lane_span(r1, mode, a, len);
+      if (mode != kSegment && wmax <= kUnroll) seg_gather<X, kUnroll>(rc + ((a + off) & kRingMask), len, wmax, x, xn);
+      if (aux != nullptr && holds_result(mode, r1)) an = aux[r1.row];
     }
     // multiply-adds of step s
     const int mode = m0 & 3;
@@ -554,18 +572,21 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         Acc tot;
         if constexpr (sizeof(Acc) == 8) tot = warp_sum(seg_acc);
         else tot = warp_sum_f(seg_acc);
-        if (lane == 0) epi(d0.x, tot);
+        if (lane == 0) epi(d0.x, tot, aux != nullptr ? aux[d0.x] : 0.0);
       }
     } else {
-      const int p0 = rpos(lw0);
-      const Acc part = lw0.wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv + p0, lw0.len, lw0.wmax, xc)
-                                           : seg_dot_loop<T, X, Acc>(rv + p0, rc + p0, lw0.len, x);
+      const int wmax = (m0 >> kWmaxShift) & 0xff;
+      int a, len;
+      lane_span(r0, mode, a, len);
+      const int p0 = (a + off) & kRingMask;
+      const Acc part = wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv + p0, len, wmax, xc)
+                                       : seg_dot_loop<T, X, Acc>(rv + p0, rc + p0, len, x);
       if (mode == kPairPerRow) {
         // first half + second half: the same value in both lanes (commutative add)
         const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);
-        if ((lane & 1) == 0 && lw0.row >= 0) epi(lw0.row, sum);
-      } else if (lw0.row >= 0) {
-        epi(lw0.row, part);
+        if (holds_result(mode, r0)) epi(r0.row, sum, ac);
+      } else if (holds_result(mode, r0)) {
+        epi(r0.row, part, ac);
       }
     }
     // release the pieces that end before step s+1's first entry and refill
@@ -579,11 +600,12 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         stream_fill<T>(sm, ws, val, A.col_idx);
       }
     }
-    d0 = d1; m0 = m1; lw0 = lw1;
-    d1 = d2; m1 = m2; lw1 = lw2;
+    d0 = d1; m0 = m1; r0 = r1;
+    d1 = d2; m1 = m2; r1 = r2;
     d2 = d3; m2 = m3;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) xc[u] = xn[u];
+    ac = an;
   }
   stream_end_pass<Tn>(sm, ws, next_val, A.col_idx);
   return true;

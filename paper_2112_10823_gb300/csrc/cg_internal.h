@@ -46,6 +46,9 @@ enum StepMode : int32_t {
 // Flags of a kSegment step (stored above the mode bits).
 constexpr int32_t kSegFirst = 4;
 constexpr int32_t kSegLast = 8;
+// Bits 8..15 of a step's mode word: the longest per-lane segment of the step
+// (precomputed so that the lanes need no warp reduction to bound their loops).
+constexpr int kWmaxShift = 8;
 
 // Device view of a CSR matrix with its step partition.
 struct DevCsr {

@@ -94,8 +94,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   // ---- setup: r = b - A x, p = r, rho = r.r, ||b||^2
   double acc_rr = 0.0, acc_bb = 0.0;
   {
-    auto epi = [&](int i, double s) {
-      const double bi = b[i];
+    auto epi = [&](int i, double s, double bi) {
       const double ri = bi - s;
       r[i] = ri;
       p[i] = ri;
@@ -104,8 +103,8 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       acc_bb = fma(bi, bi, acc_bb);
     };
     bool ok;
-    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val32, lim);
-    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val, lim);
+    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val32, lim);
+    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val, lim);
     if (!ok) { solve_fail(sm, rs, P); return; }
   }
   double rho, bnorm2;
@@ -135,18 +134,18 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     double acc_g = 0.0;
     bool ok;
     if constexpr (kMixed) {
-      auto epi = [&](int i, float s) {
+      auto epi = [&](int i, float s, double pi) {
         const double qi = static_cast<double>(s);
         q[i] = qi;
-        acc_g = fma(p[i], qi, acc_g);
+        acc_g = fma(pi, qi, acc_g);
       };
-      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, p32, epi, A.val32, lim);
+      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, p32, p, epi, A.val32, lim);
     } else {
-      auto epi = [&](int i, double s) {
+      auto epi = [&](int i, double s, double pi) {
         q[i] = s;
-        acc_g = fma(p[i], s, acc_g);
+        acc_g = fma(pi, s, acc_g);
       };
-      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, p, epi, A.val, lim);
+      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, p, p, epi, A.val, lim);
     }
     double gamma;
     if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, rs, P); return; }
@@ -189,12 +188,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       for (int i = row0 + tid; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
       if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
       double acc_t = 0.0;
-      auto epi = [&](int i, double s) {
-        const double ri = b[i] - s;
+      auto epi = [&](int i, double s, double bi) {
+        const double ri = bi - s;
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
       };
-      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, A.val32, lim) ||
+      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val32, lim) ||
           !allreduce(acc_t, rho_new)) {
         solve_fail(sm, rs, P);
         return;
@@ -252,12 +251,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
   double acc_t = 0.0;
   {
-    auto epi = [&](int i, double s) {
-      const double d = b[i] - s;
+    auto epi = [&](int i, double s, double bi) {
+      const double d = bi - s;
       acc_t = fma(d, d, acc_t);
     };
     double tsum;
-    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, epi, no_next, lim) ||
+    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, no_next, lim) ||
         !allreduce(acc_t, tsum)) {
       solve_fail(sm, rs, P);
       return;
@@ -281,9 +280,9 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A
   const RingSmem sm{smem_raw};
   WarpStream ws;
   stream_init(sm, ws, A);
-  auto epi = [&](int i, double s) { y[i] = s; };
+  auto epi = [&](int i, double s, double) { y[i] = s; };
   const double* const no_next = nullptr;
-  if (!spmv_pass<double, double, double>(sm, ws, A, A.val, x, epi, no_next, 2000000000ull)) {
+  if (!spmv_pass<double, double, double>(sm, ws, A, A.val, x, nullptr, epi, no_next, 2000000000ull)) {
     stream_drain(sm, ws, 2000000000ull);
     if ((threadIdx.x & 31) == 0) atomicExch(err, kETIMEOUT);
   }
