@@ -421,24 +421,49 @@ __device__ __forceinline__ void stream_drain(const RingSmem& sm, WarpStream& ws,
 
 // Gathers of one lane's row segment: xv[u] = x[cp[u]] for its len entries,
 // cp pointing at the segment's column indices in the ring (contiguous thanks
-// to the mirror).  Called by all 32 lanes (len = 0 for lanes without a row);
-// wmax is the warp's longest segment, so no instruction is issued for a slot
-// no lane needs.
-template <typename X, int U>
-__device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
+// to the mirror).  N is the step's longest per-lane segment (lanes with a
+// shorter segment, or none, are predicated off for the tail), so the code is
+// branch-free and no instruction is issued for a slot no lane needs.
+template <typename X, int N, int U>
+__device__ __forceinline__ void seg_gather_n(const int32_t* cp, int len, const X* x, X (&xv)[U]) {
 #pragma unroll
-  for (int u = 0; u < U; ++u)
-    if (u < wmax && u < len) xv[u] = x[cp[u]];
+  for (int u = 0; u < N; ++u)
+    if (u < len) xv[u] = x[cp[u]];
 }
 
 // Multiply-adds of a gathered segment, in storage order, with FMA.
-template <typename T, typename X, typename Acc, int U>
-__device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U]) {
+template <typename T, typename X, typename Acc, int N, int U>
+__device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U]) {
   Acc s = Acc(0);
 #pragma unroll
-  for (int u = 0; u < U; ++u)
-    if (u < wmax && u < len) s = fma(Acc(vp[u]), Acc(xv[u]), s);
+  for (int u = 0; u < N; ++u)
+    if (u < len) s = fma(Acc(vp[u]), Acc(xv[u]), s);
   return s;
+}
+
+// Dispatch on the step's longest per-lane segment (1..U): one branch per step.
+#define CGK_SEG_CASES(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+
+template <typename X, int U>
+__device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
+  static_assert(U == 16, "dispatch covers 1..16");
+  switch (wmax) {
+#define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
+    CGK_SEG_CASES(CGK_G)
+#undef CGK_G
+    default: break;
+  }
+}
+
+template <typename T, typename X, typename Acc, int U>
+__device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U]) {
+  static_assert(U == 16, "dispatch covers 1..16");
+  switch (wmax) {
+#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv);
+    CGK_SEG_CASES(CGK_F)
+#undef CGK_F
+    default: return Acc(0);
+  }
 }
 
 // A segment longer than the unrolled capacity (up to kMirror entries: rows of
