@@ -130,9 +130,10 @@ int64_t cost_split(const std::vector<int32_t>& rp, int64_t lo_row, int64_t hi_ro
 }
 
 void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partition& P) {
+  const int64_t kPairMax = 2 * cgk::kLaneMax;
   while (row < end) {
     const int64_t len0 = rp[row + 1] - rp[row];
-    if (len0 > 64) {  // a long row: segments through the ring
+    if (len0 > kPairMax) {  // a long row: segments through the ring
       for (int64_t e = rp[row]; e < rp[row + 1]; e += cgk::kSegNnz) {
         const int64_t e1 = std::min<int64_t>(e + cgk::kSegNnz, rp[row + 1]);
         int32_t m = cgk::kSegment;
@@ -149,16 +150,16 @@ void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partit
     int64_t cnt = 0, maxlen = 0;
     while (row < end) {
       const int64_t len = rp[row + 1] - rp[row];
-      if (len > 64 || cnt + len > cgk::kStepNnz) break;
+      if (len > kPairMax || cnt + len > cgk::kStepNnz) break;
       const int64_t nm = std::max(maxlen, len);
-      const int64_t cap = nm <= 16 ? 32 : 16;
+      const int64_t cap = nm <= cgk::kLaneMax ? 32 : 16;
       if (row - start + 1 > cap) break;
       cnt += len;
       maxlen = nm;
       ++row;
     }
     P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
-    const bool lane_mode = maxlen <= 16;
+    const bool lane_mode = maxlen <= cgk::kLaneMax;
     const int64_t wmax = lane_mode ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
     P.step_mode.push_back((lane_mode ? cgk::kLanePerRow : cgk::kPairPerRow) |
                           static_cast<int32_t>(wmax << cgk::kWmaxShift));

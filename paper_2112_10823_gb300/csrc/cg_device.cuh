@@ -441,12 +441,13 @@ __device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U])
   return s;
 }
 
-// Dispatch on the step's longest per-lane segment (1..U): one branch per step.
-#define CGK_SEG_CASES(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+// Dispatch on the step's longest per-lane segment (1..32): one branch per step.
+#define CGK_SEG_CASES(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) \
+  M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
 
 template <typename X, int U>
 __device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
-  static_assert(U == 16, "dispatch covers 1..16");
+  static_assert(U == 32, "dispatch covers 1..32");
   switch (wmax) {
 #define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
     CGK_SEG_CASES(CGK_G)
@@ -457,7 +458,7 @@ __device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax,
 
 template <typename T, typename X, typename Acc, int U>
 __device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U]) {
-  static_assert(U == 16, "dispatch covers 1..16");
+  static_assert(U == 32, "dispatch covers 1..32");
   switch (wmax) {
 #define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv);
     CGK_SEG_CASES(CGK_F)
@@ -523,17 +524,14 @@ __device__ __forceinline__ void lane_span(const LaneRaw& r, int mode, int& a, in
   }
 }
 
-constexpr int kUnroll = 16;  // entries per lane gathered at once
-
 // The product over this warp's steps with values `val` (type T), gathering x;
 // each row's result goes to epi(i, yi, aux[i]) from one lane (aux[i] = 0 when
-// aux is nullptr).  Software-pipelined: the gathers of step s+1 and its aux
-// values are issued before the multiply-adds of step s, the row pointers two
-// steps ahead and the descriptors three steps ahead, so within a step only
-// FP64 work and shared-memory reads remain.  The pass starts from the pieces
-// prefetched for it (if any) and ends by prefetching the first pieces of the
-// next pass (next_val of type Tn; nullptr for none).  Returns false
-// (uniformly over the warp) if a wait gave up.
+// aux is nullptr).  Step descriptors are loaded two steps ahead, row pointers
+// and aux values one step ahead, so a step's own latency is one round of
+// gathers, which the FMA chains of the SM's other warps cover.  The pass
+// starts from the pieces prefetched for it (if any) and ends by prefetching
+// the first pieces of the next pass (next_val of type Tn; nullptr for none).
+// Returns false (uniformly over the warp) if a wait gave up.
 template <typename T, typename X, typename Acc, typename Tn, typename Epi>
 __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, const DevCsr& A, const T* val,
                                           const X* x, const double* aux, Epi& epi, const Tn* next_val,
@@ -544,9 +542,6 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
   const int32_t* row_ptr = A.row_ptr;
   if (!stream_begin_pass<T>(sm, ws, val, A.col_idx, limit_ns)) return false;
   const int off = static_cast<int>((ws.gbase % kSlots) * kPiece) - ws.kb;  // ring pos = (k + off) & mask
-  auto wait_step = [&](int4 dd) -> bool {
-    return dd.w <= dd.z || stream_wait_upto(sm, ws, ((dd.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns);
-  };
   // descriptor index clamped to the array (two sentinels follow the last step)
   auto sd = [&](int k) { return k < A.nsteps + 2 ? k : A.nsteps + 1; };
   auto holds_result = [&](int mode, const LaneRaw& r) {
@@ -554,38 +549,19 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
   };
   Acc seg_acc = Acc(0);
   int s = ws.s0;
-  int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + 1)], d2 = A.step[sd(s + 2)];
-  int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + 1)], m2 = A.step_mode[sd(s + 2)];
+  int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + 1)];
+  int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + 1)];
   LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < ws.s1);
-  LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, s + 1 < ws.s1);
-  X xc[kUnroll];      // gathered x of step s
-  double ac = 0.0;    // aux value of this lane's row in step s
-  if (s < ws.s1) {
-    if (!wait_step(d0)) return false;
-    const int mode = m0 & 3, wmax = (m0 >> kWmaxShift) & 0xff;
-    int a, len;
-    lane_span(r0, mode, a, len);
-    if (mode != kSegment && wmax <= kUnroll) seg_gather<X, kUnroll>(rc + ((a + off) & kRingMask), len, wmax, x, xc);
-    if (aux != nullptr && holds_result(mode, r0)) ac = aux[r0.row];
-  }
+  double a0 = (aux != nullptr && s < ws.s1 && holds_result(m0 & 3, r0)) ? aux[r0.row] : 0.0;
   for (; s < ws.s1; ++s) {
     const bool has1 = s + 1 < ws.s1;
-    // prefetch: descriptor of step s+3, row pointers of step s+2
-    const int4 d3 = A.step[sd(s + 3)];
-    const int m3 = A.step_mode[sd(s + 3)];
-    const LaneRaw r2 = lane_raw(row_ptr, d2, m2 & 3, s + 2 < ws.s1);
-    // gathers and aux values of step s+1 (its entries must be in the ring)
-    X xn[kUnroll];
-    double an = 0.0;
-    if (has1) {
-      if (!wait_step(d1)) return false;
-      const int mode = m1 & 3, wmax = (m1 >> kWmaxShift) & 0xff;
-      int a, len;
-      lane_span(r1, mode, a, len);
-      if (mode != kSegment && wmax <= kUnroll) seg_gather<X, kUnroll>(rc + ((a + off) & kRingMask), len, wmax, x, xn);
-      if (aux != nullptr && holds_result(mode, r1)) an = aux[r1.row];
-    }
-    // multiply-adds of step s
+    // prefetch: descriptor of step s+2, row pointers and aux value of step s+1
+    const int4 d2 = A.step[sd(s + 2)];
+    const int m2 = A.step_mode[sd(s + 2)];
+    const LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, has1);
+    const double a1 = (aux != nullptr && has1 && holds_result(m1 & 3, r1)) ? aux[r1.row] : 0.0;
+    // this step's entries must be in the ring
+    if (d0.w > d0.z && !stream_wait_upto(sm, ws, ((d0.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns)) return false;
     const int mode = m0 & 3;
     if (mode == kSegment) {
       if (m0 & kSegFirst) seg_acc = Acc(0);
@@ -604,14 +580,15 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
       int a, len;
       lane_span(r0, mode, a, len);
       const int p0 = (a + off) & kRingMask;
-      const Acc part = wmax <= kUnroll ? seg_fma<T, X, Acc, kUnroll>(rv + p0, len, wmax, xc)
-                                       : seg_dot_loop<T, X, Acc>(rv + p0, rc + p0, len, x);
+      X xv[kLaneMax];
+      seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
+      const Acc part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv);
       if (mode == kPairPerRow) {
         // first half + second half: the same value in both lanes (commutative add)
         const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);
-        if (holds_result(mode, r0)) epi(r0.row, sum, ac);
+        if (holds_result(mode, r0)) epi(r0.row, sum, a0);
       } else if (holds_result(mode, r0)) {
-        epi(r0.row, part, ac);
+        epi(r0.row, part, a0);
       }
     }
     // release the pieces that end before step s+1's first entry and refill
@@ -625,12 +602,8 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         stream_fill<T>(sm, ws, val, A.col_idx);
       }
     }
-    d0 = d1; m0 = m1; r0 = r1;
-    d1 = d2; m1 = m2; r1 = r2;
-    d2 = d3; m2 = m3;
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) xc[u] = xn[u];
-    ac = an;
+    d0 = d1; m0 = m1; r0 = r1; a0 = a1;
+    d1 = d2; m1 = m2;
   }
   stream_end_pass<Tn>(sm, ws, next_val, A.col_idx);
   return true;

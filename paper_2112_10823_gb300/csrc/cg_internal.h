@@ -25,22 +25,22 @@ constexpr int kRingMask = kRing - 1;
 // slot 0 is copied there as well, so a row segment of up to kMirror entries
 // starting anywhere in the ring reads contiguously, without wrapping.
 constexpr int kMirror = 32;
-// A step is what a warp computes at once: up to 32 rows of <= 16 entries
-// (one lane per row), up to 16 rows of <= 64 entries (two lanes per row), or
+// A step is what a warp computes at once: up to 32 rows of <= 32 entries
+// (one lane per row), up to 16 rows of 33..64 entries (two lanes per row), or
 // a segment of <= kSegNnz entries of one longer row (lanes stride the
 // segment; the row's sum is completed at its last segment).  A step holds at
-// most kStepNnz entries: a quarter of the ring, so that two consecutive steps
-// (the one being multiplied and the next, whose gathers are already in
-// flight) stay resident while later pieces stream in.
-constexpr int kStepNnz = kRing / 4;
+// most kStepNnz entries: half the ring, so later pieces stream in while it is
+// computed.
+constexpr int kStepNnz = kRing / 2;
 constexpr int kSegNnz = kPiece;
+constexpr int kLaneMax = 32;  // longest row computed by a single lane
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
 constexpr int kPadEntries = 8;
 
 enum StepMode : int32_t {
-  kLanePerRow = 0,   // lane l computes row r0 + l
-  kPairPerRow = 1,   // lanes 2t, 2t+1 split row r0 + t
+  kLanePerRow = 0,   // lane l computes row r0 + l (rows of <= kLaneMax entries)
+  kPairPerRow = 1,   // lanes 2t, 2t+1 split row r0 + t (rows of <= 2 kLaneMax entries)
   kSegment = 2,      // entries [e0, e1) of row r0; lanes stride them
 };
 // Flags of a kSegment step (stored above the mode bits).
