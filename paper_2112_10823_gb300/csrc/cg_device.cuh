@@ -50,12 +50,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Bulk prefetch of global memory into L2 (no shared memory, no completion).
-// src 16-byte aligned, bytes a non-zero multiple of 16.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -367,21 +361,6 @@ __device__ __forceinline__ bool stream_wait_upto(const RingSmem& sm, WarpStream&
   return true;
 }
 
-// Pieces prefetched into L2 ahead of the ring's issue frontier, so that the
-// ring's copies hit L2 instead of waiting on DRAM.
-constexpr int kL2Ahead = 4;
-
-template <typename T>
-__device__ __forceinline__ void stream_prefetch_l2(const WarpStream& ws, int j, const T* val, const int32_t* col) {
-  if (j >= ws.npieces) return;
-  const int e0 = ws.kb + j * kPiece;
-  int e1 = e0 + kPiece;
-  const int ke4 = (ws.ke + 3) & ~3;
-  if (e1 > ke4) e1 = ke4;
-  bulk_prefetch_l2(val + e0, static_cast<uint32_t>(e1 - e0) * sizeof(T));
-  bulk_prefetch_l2(col + e0, static_cast<uint32_t>(e1 - e0) * 4u);
-}
-
 // Keep the warp's ring full.  The lanes of the warp must be done reading the
 // released slots (a __syncwarp precedes every call).
 template <typename T>
@@ -389,10 +368,7 @@ __device__ __forceinline__ void stream_fill(const RingSmem& sm, WarpStream& ws, 
   int lim = ws.released + kSlots;
   if (lim > ws.npieces) lim = ws.npieces;
   if ((threadIdx.x & 31) == 0)
-    for (int j = ws.issued; j < lim; ++j) {
-      stream_issue<T>(sm, ws, ws.gbase, j, val, col);
-      stream_prefetch_l2<T>(ws, j + kL2Ahead, val, col);
-    }
+    for (int j = ws.issued; j < lim; ++j) stream_issue<T>(sm, ws, ws.gbase, j, val, col);
   if (lim > ws.issued) ws.issued = lim;
 }
 
@@ -413,8 +389,6 @@ __device__ __forceinline__ bool stream_begin_pass(const RingSmem& sm, WarpStream
   ws.pre_count = 0;
   ws.pre_type = 0;
   __syncwarp();
-  if ((threadIdx.x & 31) == 0)
-    for (int j = ws.issued; j < ws.issued + kL2Ahead; ++j) stream_prefetch_l2<T>(ws, j, val, col);
   stream_fill<T>(sm, ws, val, col);
   return true;
 }
