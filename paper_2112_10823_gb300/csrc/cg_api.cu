@@ -34,7 +34,7 @@ struct cg_ctx {
   float* d_val32 = nullptr;
   int4* d_step = nullptr;
   int32_t* d_step_mode = nullptr;
-  int32_t* d_warp_step = nullptr;
+  int32_t* d_block_step = nullptr;
   int32_t* d_block_row = nullptr;
   double* d_r = nullptr;
   double* d_p = nullptr;
@@ -101,8 +101,8 @@ bool is_device_ptr(const void* p) {
 
 // Row partition of the persistent kernels.  Rows are split into `nblocks`
 // contiguous CTA ranges of about equal cost (stored entries + kRowCost per
-// row, the per-row vector work), each CTA range into kWarps warp ranges the
-// same way, and each warp range into steps (see cg_internal.h): up to 32 rows
+// row, the per-row vector work), and each CTA range into steps (see
+// cg_internal.h): up to 32 rows
 // of <= 16 entries, up to 16 rows of <= 64 entries, or segments of <= kSegNnz
 // entries of a longer row, never more than kStepNnz entries per step.  Two
 // sentinel steps follow the last one (the kernels read descriptors ahead).
@@ -111,7 +111,7 @@ constexpr int64_t kRowCost = 6;
 struct Partition {
   std::vector<int4> step;
   std::vector<int32_t> step_mode;
-  std::vector<int32_t> warp_step;
+  std::vector<int32_t> block_step;
   std::vector<int32_t> block_row;
 };
 
@@ -169,20 +169,15 @@ void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partit
 void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P) {
   P.step.clear();
   P.step_mode.clear();
-  P.warp_step.assign(static_cast<size_t>(nblocks) * cgk::kWarps + 1, 0);
+  P.block_step.assign(static_cast<size_t>(nblocks) + 1, 0);
   P.block_row.assign(static_cast<size_t>(nblocks) + 1, 0);
   for (int b = 0; b <= nblocks; ++b) P.block_row[b] = static_cast<int32_t>(cost_split(rp, 0, n, b, nblocks));
   P.block_row[nblocks] = static_cast<int32_t>(n);
   for (int b = 0; b < nblocks; ++b) {
-    const int64_t r0 = P.block_row[b], r1 = P.block_row[b + 1];
-    for (int w = 0; w < cgk::kWarps; ++w) {
-      P.warp_step[static_cast<size_t>(b) * cgk::kWarps + w] = static_cast<int32_t>(P.step.size());
-      const int64_t a = cost_split(rp, r0, r1, w, cgk::kWarps);
-      const int64_t z = (w == cgk::kWarps - 1) ? r1 : cost_split(rp, r0, r1, w + 1, cgk::kWarps);
-      warp_steps(rp, a, z, P);
-    }
+    P.block_step[b] = static_cast<int32_t>(P.step.size());
+    warp_steps(rp, P.block_row[b], P.block_row[b + 1], P);
   }
-  P.warp_step[static_cast<size_t>(nblocks) * cgk::kWarps] = static_cast<int32_t>(P.step.size());
+  P.block_step[nblocks] = static_cast<int32_t>(P.step.size());
   for (int t = 0; t < 2; ++t) {  // sentinels
     P.step.push_back(make_int4(static_cast<int>(n), static_cast<int>(n), rp[n], rp[n]));
     P.step_mode.push_back(cgk::kLanePerRow);
@@ -197,7 +192,7 @@ cgk::DevCsr dev_view(const cg_ctx* h) {
   A.val32 = h->d_val32;
   A.step = h->d_step;
   A.step_mode = h->d_step_mode;
-  A.warp_step = h->d_warp_step;
+  A.block_step = h->d_block_step;
   A.block_row = h->d_block_row;
   A.n = static_cast<int32_t>(h->n);
   A.nsteps = h->nsteps;
@@ -351,7 +346,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(dalloc(h, &h->d_val, nnz + pad), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_step, part.step.size()), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_step_mode, part.step_mode.size()), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_warp_step, part.warp_step.size()), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_block_step, part.block_step.size()), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_block_row, part.block_row.size()), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_r, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_p, n), "cg_create: cudaMalloc");
@@ -387,7 +382,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(cudaMemcpy(h->d_step_mode, part.step_mode.data(), sizeof(int32_t) * part.step_mode.size(),
                     cudaMemcpyHostToDevice),
          "cg_create: upload");
-  CG_TRY(cudaMemcpy(h->d_warp_step, part.warp_step.data(), sizeof(int32_t) * part.warp_step.size(),
+  CG_TRY(cudaMemcpy(h->d_block_step, part.block_step.data(), sizeof(int32_t) * part.block_step.size(),
                     cudaMemcpyHostToDevice),
          "cg_create: upload");
   CG_TRY(cudaMemcpy(h->d_block_row, part.block_row.data(), sizeof(int32_t) * part.block_row.size(),

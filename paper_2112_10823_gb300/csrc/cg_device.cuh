@@ -76,6 +76,32 @@ __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) {
   return *reinterpret_cast<const volatile int32_t*>(p);
 }
 
+// Barrier of the consumer warps only (named barrier 1): the producer warp of
+// a solve CTA never takes part in CTA-wide synchronisation.
+__device__ __forceinline__ void cta_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+
+// AND of a per-thread condition over the consumer warps (named barrier 1).
+// Every consumer thread must reach it; used after each product pass so that a
+// warp that gave up on a wait and the others leave the kernel together.
+__device__ __forceinline__ bool cta_and(bool v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<int>(v)), "n"(kConsumers)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // ------------------------------------------------------------ reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -127,10 +153,11 @@ struct FxScratch {
 // whatever the order of arrival), and the total is rounded once back to FP64.
 // Zero and subnormal values count as zero; an infinite or NaN value makes the
 // sum NaN.  Thread 0 converts the total; every thread receives it through
-// shared memory.  Requires blockDim.x == kBlock and K * kBlock <= 1024.
+// shared memory.  Called by the kConsumers consumer threads (K * kConsumers
+// <= 1024).
 template <int K>
 __device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* sc) {
-  static_assert(K * kBlock <= 1024, "fixed-point headroom is 10 bits");
+  static_assert(K * kConsumers <= 1024, "fixed-point headroom is 10 bits");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long bits[K];
   int e[K];
@@ -144,12 +171,12 @@ __device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* 
   }
   const unsigned int ew = __reduce_max_sync(0xffffffffu, static_cast<unsigned int>(emax));
   const int nfw = __any_sync(0xffffffffu, nfl);
-  __syncthreads();  // earlier users of sc are done
+  cta_sync();  // earlier users of sc are done
   if (lane == 0) {
     sc->e[warp] = static_cast<int32_t>(ew);
     sc->nf[warp] = nfw;
   }
-  __syncthreads();
+  cta_sync();
   int E = 0, nf = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
@@ -171,7 +198,7 @@ __device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
   if (lane == 0) sc->m[warp] = m;
-  __syncthreads();
+  cta_sync();
   if (threadIdx.x == 0) {
     long long tot = 0;
 #pragma unroll
@@ -182,7 +209,7 @@ __device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* 
     else r = ldexp(static_cast<double>(tot), E - 1074);
     sc->result = r;
   }
-  __syncthreads();
+  cta_sync();
   return sc->result;
 }
 
@@ -206,7 +233,7 @@ struct GridBarrier {
 
   // All threads call; the CTA's writes before this point are published.
   __device__ __forceinline__ void arrive(SolveCtrl* ctrl) {
-    __syncthreads();
+    cta_sync();
     target += gridDim.x;
     if (threadIdx.x == 0) {
       __threadfence();
@@ -236,7 +263,7 @@ struct GridBarrier {
       __threadfence();
       *flag_smem = ok;
     }
-    __syncthreads();
+    cta_sync();
     return *flag_smem != 0;
   }
 
@@ -249,175 +276,129 @@ struct GridBarrier {
 
 // ------------------------------------------------------ streamed CSR product
 
-// Shared memory of a CTA: one ring per warp (values sized for FP64, the FP32
-// product uses the first half of a warp's value ring), the column-index
-// rings, each followed by its kMirror-entry mirror, kSlots mbarriers per warp,
-// reduction scratch and broadcast words.
+// Shared memory of a solve or product CTA: the value ring (sized for FP64;
+// FP32 values use its first half) and the column-index ring, each followed by
+// its kMirror-entry mirror, the full/empty mbarriers of every slot, reduction
+// scratch and a few words (stop flag, broadcast scalars).
 struct RingSmem {
   static constexpr int kRingAlloc = kRing + kMirror;
-  static constexpr size_t kValBytes = sizeof(double) * kRingAlloc * kWarps;
-  static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc * kWarps;
-  static constexpr size_t kBarOff = kValBytes + kColBytes;
-  static constexpr size_t kRedOff = kBarOff + 8 * kSlots * kWarps;
-  static constexpr size_t kRedBytes = sizeof(double) * (kBlock + 8);
-  static constexpr size_t kFxOff = kRedOff + kRedBytes;
+  static constexpr size_t kValBytes = sizeof(double) * kRingAlloc;
+  static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc;
+  static constexpr size_t kBarOff = (kValBytes + kColBytes + 15) & ~size_t(15);
+  static constexpr size_t kFxOff = kBarOff + 16 * kSlots;
   static constexpr size_t kFxBytes = (sizeof(FxScratch) + 15) & ~size_t(15);
   static constexpr size_t kMiscOff = kFxOff + kFxBytes;
   static constexpr size_t kBytes = kMiscOff + 64;
 
   unsigned char* base;
   template <typename T>
-  __device__ T* val(int w) const { return reinterpret_cast<T*>(base + sizeof(double) * kRingAlloc * w); }
-  __device__ int32_t* col(int w) const { return reinterpret_cast<int32_t*>(base + kValBytes) + kRingAlloc * w; }
-  __device__ uint64_t* bar(int w, int s) const {
-    return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots * w + s;
-  }
-  __device__ double* red() const { return reinterpret_cast<double*>(base + kRedOff); }
+  __device__ T* val() const { return reinterpret_cast<T*>(base); }
+  __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + kValBytes); }
+  __device__ uint64_t* full(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + s; }
+  __device__ uint64_t* empty(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots + s; }
   __device__ FxScratch* fx() const { return reinterpret_cast<FxScratch*>(base + kFxOff); }
   __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + kMiscOff); }
+  __device__ int32_t* stop() const { return reinterpret_cast<int32_t*>(base + kMiscOff + 4); }
   __device__ double* scalars() const { return reinterpret_cast<double*>(base + kMiscOff + 16); }
 };
 
-// State of one warp's matrix stream; in registers, identical in all lanes.
-// Pieces are numbered globally (across passes): the slot of global piece g
-// is g % kSlots and the mbarrier phase it completes is (g / kSlots) & 1.
-struct WarpStream {
-  int kb = 0;            // first entry of the warp's range, rounded down to a multiple of 4
-  int ke = 0;            // end of the warp's entry range
-  int npieces = 0;       // pieces per pass
-  int s0 = 0, s1 = 0;    // the warp's steps [s0, s1)
-  uint32_t gbase = 0;    // global number of piece 0 of the current pass
-  int issued = 0;        // pieces of the current pass issued
-  int waited = 0;        // pieces of the current pass seen complete
-  int released = 0;      // pieces of the current pass whose slots may be refilled
-  int pre_type = 0;      // value size (4 or 8) of pieces prefetched for the next pass, 0 = none
-  int pre_count = 0;     // pieces of the next pass already issued
+// The CTA's part of the matrix stream (identical in every thread).  Pieces
+// are numbered globally across passes (piece j of pass k is k * npieces + j);
+// global piece g sits in slot g % kSlots and completes phase g / kSlots of
+// that slot's full barrier.
+struct CtaStream {
+  int kb = 0;        // first entry of the CTA's range, rounded down to a multiple of 4
+  int ke = 0;        // end of the CTA's entry range
+  int npieces = 0;   // pieces per pass
+  int s0 = 0, s1 = 0;  // the CTA's steps [s0, s1)
 };
 
-// Set up the rings of all warps (all threads call) and this warp's stream.
-__device__ __forceinline__ void stream_init(const RingSmem& sm, WarpStream& ws, const DevCsr& A) {
-  const int w = threadIdx.x >> 5;
-  if (threadIdx.x < kWarps * kSlots) mbar_init(sm.bar(threadIdx.x / kSlots, threadIdx.x % kSlots), 1);
-  if (threadIdx.x == 0) fence_mbar_init();
+// Initialise the barriers (all threads of the CTA call, then a full barrier).
+__device__ __forceinline__ void stream_setup(const RingSmem& sm, CtaStream& cs, const DevCsr& A) {
+  if (threadIdx.x < kSlots) {
+    mbar_init(sm.full(threadIdx.x), 1);
+    mbar_init(sm.empty(threadIdx.x), kConsumerWarps);
+  }
+  if (threadIdx.x == 0) {
+    *sm.stop() = 0;
+    fence_mbar_init();
+  }
   __syncthreads();
-  const int gw = blockIdx.x * kWarps + w;
-  ws.s0 = A.warp_step[gw];
-  ws.s1 = A.warp_step[gw + 1];
-  if (ws.s1 > ws.s0) {
-    ws.kb = A.step[ws.s0].z & ~3;
-    ws.ke = A.step[ws.s1 - 1].w;
-    ws.npieces = (ws.ke - ws.kb + kPiece - 1) >> kPieceLog;
+  cs.s0 = A.block_step[blockIdx.x];
+  cs.s1 = A.block_step[blockIdx.x + 1];
+  if (cs.s1 > cs.s0) {
+    cs.kb = A.step[cs.s0].z & ~3;
+    cs.ke = A.step[cs.s1 - 1].w;
+    cs.npieces = (cs.ke - cs.kb + kPiece - 1) >> kPieceLog;
   }
 }
 
-// Issue piece j of the pass starting at gbase (values of type T).  Lane 0.
-template <typename T>
-__device__ __forceinline__ void stream_issue(const RingSmem& sm, const WarpStream& ws, uint32_t gbase, int j,
-                                             const T* val, const int32_t* col) {
-  const int w = threadIdx.x >> 5;
-  const int e0 = ws.kb + j * kPiece;
-  int e1 = e0 + kPiece;
-  const int ke4 = (ws.ke + 3) & ~3;  // whole 16-byte groups (<= 3 padding entries)
-  if (e1 > ke4) e1 = ke4;
-  const int slot = static_cast<int>((gbase + static_cast<uint32_t>(j)) % kSlots);
-  const int pos = slot * kPiece;
-  const uint32_t bv = static_cast<uint32_t>(e1 - e0) * sizeof(T);
-  const uint32_t bc = static_cast<uint32_t>(e1 - e0) * 4u;
-  // slot 0 also fills the mirror behind the ring end with its first entries
-  const int nm = slot == 0 ? (e1 - e0 < kMirror ? e1 - e0 : kMirror) : 0;  // a multiple of 4
-  const uint32_t mv = static_cast<uint32_t>(nm) * sizeof(T), mc = static_cast<uint32_t>(nm) * 4u;
-  fence_proxy_async_smem();
-  mbar_arrive_expect_tx(sm.bar(w, slot), bv + bc + mv + mc);
-  bulk_g2s(sm.val<T>(w) + pos, val + e0, bv, sm.bar(w, slot));
-  bulk_g2s(sm.col(w) + pos, col + e0, bc, sm.bar(w, slot));
-  if (nm) {
-    bulk_g2s(sm.val<T>(w) + kRing, val + e0, mv, sm.bar(w, slot));
-    bulk_g2s(sm.col(w) + kRing, col + e0, mc, sm.bar(w, slot));
-  }
-}
-
-// Wait (bounded) for global piece g of this warp; uniform over the warp.
-__device__ __forceinline__ bool stream_wait_global(const RingSmem& sm, uint32_t g, unsigned long long limit_ns) {
-  const int w = threadIdx.x >> 5;
-  const int slot = static_cast<int>(g % kSlots);
-  const uint32_t parity = (g / kSlots) & 1u;
+// Bounded wait on an mbarrier phase; false if it gave up.  If `stop` is
+// given, also gives up as soon as *stop becomes non-zero.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns,
+                                                  const int32_t* stop) {
   uint32_t spins = 0;
   unsigned long long t0 = 0;
-  int ok = 1;
-  while (!mbar_try_wait(sm.bar(w, slot), parity)) {
+  while (!mbar_try_wait(bar, parity)) {
     if ((++spins & 63u) == 0) {
+      if (stop && ld_volatile_i32(stop)) return false;
       const unsigned long long now = global_timer_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > limit_ns) { ok = 0; break; }
+      else if (now - t0 > limit_ns) return false;
     }
   }
-  return __all_sync(0xffffffffu, ok) != 0;
-}
-
-__device__ __forceinline__ bool stream_wait_upto(const RingSmem& sm, WarpStream& ws, int upto,
-                                                 unsigned long long limit_ns) {
-  for (; ws.waited < upto; ++ws.waited)
-    if (!stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(ws.waited), limit_ns)) return false;
   return true;
 }
 
-// Keep the warp's ring full.  The lanes of the warp must be done reading the
-// released slots (a __syncwarp precedes every call).
+// Producer (one lane of the producer warp): stream the CTA's range pass after
+// pass (max_passes < 0: until told to stop) with values of type T.  Before
+// refilling a slot it waits for every consumer warp to release the slot's
+// previous piece.  On stop it waits for its copies still in flight, so no
+// bulk copy lands after the CTA is gone.  Returns false on a timeout.
 template <typename T>
-__device__ __forceinline__ void stream_fill(const RingSmem& sm, WarpStream& ws, const T* val, const int32_t* col) {
-  int lim = ws.released + kSlots;
-  if (lim > ws.npieces) lim = ws.npieces;
-  if ((threadIdx.x & 31) == 0)
-    for (int j = ws.issued; j < lim; ++j) stream_issue<T>(sm, ws, ws.gbase, j, val, col);
-  if (lim > ws.issued) ws.issued = lim;
-}
-
-// Start a pass over values of type T: adopt pieces prefetched for it, or
-// first wait out prefetched pieces of the other type and skip past them.
-template <typename T>
-__device__ __forceinline__ bool stream_begin_pass(const RingSmem& sm, WarpStream& ws, const T* val,
-                                                  const int32_t* col, unsigned long long limit_ns) {
-  if (ws.pre_count > 0 && ws.pre_type != static_cast<int>(sizeof(T))) {
-    for (int j = 0; j < ws.pre_count; ++j)
-      if (!stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns)) return false;
-    ws.gbase += static_cast<uint32_t>(ws.pre_count);
-    ws.pre_count = 0;
+__device__ __forceinline__ bool producer_loop(const RingSmem& sm, const CtaStream& cs, const T* val,
+                                              const int32_t* col, int max_passes, unsigned long long limit_ns) {
+  bool ok = true;
+  uint32_t g = 0;
+  if (cs.npieces > 0) {
+    const int ke4 = (cs.ke + 3) & ~3;  // copy whole 16-byte groups (<= 3 padding entries)
+    for (int pass = 0; ok && (max_passes < 0 || pass < max_passes); ++pass) {
+      for (int j = 0; j < cs.npieces; ++j, ++g) {
+        const int slot = static_cast<int>(g % kSlots);
+        if (g >= kSlots && !mbar_wait_bounded(sm.empty(slot), ((g / kSlots) - 1) & 1u, limit_ns, sm.stop())) {
+          ok = ld_volatile_i32(sm.stop()) != 0;  // a stop is the normal way out
+          goto drain;
+        }
+        const int e0 = cs.kb + j * kPiece;
+        const int e1 = e0 + kPiece < ke4 ? e0 + kPiece : ke4;
+        const int pos = slot * kPiece;
+        const uint32_t bv = static_cast<uint32_t>(e1 - e0) * sizeof(T);
+        const uint32_t bc = static_cast<uint32_t>(e1 - e0) * 4u;
+        // slot 0 also fills the mirror behind the ring end with its first entries
+        const int nm = slot == 0 ? (e1 - e0 < kMirror ? e1 - e0 : kMirror) : 0;  // a multiple of 4
+        const uint32_t mv = static_cast<uint32_t>(nm) * sizeof(T), mc = static_cast<uint32_t>(nm) * 4u;
+        mbar_arrive_expect_tx(sm.full(slot), bv + bc + mv + mc);
+        bulk_g2s(sm.val<T>() + pos, val + e0, bv, sm.full(slot));
+        bulk_g2s(sm.col() + pos, col + e0, bc, sm.full(slot));
+        if (nm) {
+          bulk_g2s(sm.val<T>() + kRing, val + e0, mv, sm.full(slot));
+          bulk_g2s(sm.col() + kRing, col + e0, mc, sm.full(slot));
+        }
+      }
+    }
   }
-  ws.issued = ws.pre_count;
-  ws.waited = 0;
-  ws.released = 0;
-  ws.pre_count = 0;
-  ws.pre_type = 0;
-  __syncwarp();
-  stream_fill<T>(sm, ws, val, col);
-  return true;
+drain:
+  // the newest piece of every slot may still be in flight
+  for (uint32_t k = g > kSlots ? g - kSlots : 0; k < g; ++k)
+    mbar_wait_bounded(sm.full(k % kSlots), (k / kSlots) & 1u, limit_ns, nullptr);
+  return ok;
 }
 
-// End a pass (all its pieces consumed); optionally issue the first pieces of
-// the next pass (values of type Tn) so they load during what follows.
-template <typename Tn>
-__device__ __forceinline__ void stream_end_pass(const RingSmem& sm, WarpStream& ws, const Tn* next_val,
-                                                const int32_t* col) {
-  ws.gbase += static_cast<uint32_t>(ws.npieces);
-  ws.issued = ws.waited = ws.released = 0;
-  ws.pre_count = 0;
-  ws.pre_type = 0;
-  if (next_val != nullptr && ws.npieces > 0) {
-    const int cnt = ws.npieces < kSlots ? ws.npieces : kSlots;
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0)
-      for (int j = 0; j < cnt; ++j) stream_issue<Tn>(sm, ws, ws.gbase, j, next_val, col);
-    ws.pre_count = cnt;
-    ws.pre_type = static_cast<int>(sizeof(Tn));
-  }
-}
-
-// Before leaving the kernel on an error path: wait (bounded) for the copies
-// this warp still has in flight.
-__device__ __forceinline__ void stream_drain(const RingSmem& sm, WarpStream& ws, unsigned long long limit_ns) {
-  for (int j = ws.waited; j < ws.issued; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
-  for (int j = 0; j < ws.pre_count; ++j) stream_wait_global(sm, ws.gbase + static_cast<uint32_t>(j), limit_ns);
-}
+// Consumer-side position of the CTA in the stream (identical in all
+// consumer threads): global number of piece 0 of the next ring pass.
+struct ConsumerCursor {
+  uint32_t gbase = 0;
+};
 
 // Gathers of one lane's row segment: xv[u] = x[cp[u]] for its len entries,
 // cp pointing at the segment's column indices in the ring (contiguous thanks
@@ -524,49 +505,71 @@ __device__ __forceinline__ void lane_span(const LaneRaw& r, int mode, int& a, in
   }
 }
 
-// The product over this warp's steps with values `val` (type T), gathering x;
-// each row's result goes to epi(i, yi, aux[i]) from one lane (aux[i] = 0 when
-// aux is nullptr).  Step descriptors are loaded two steps ahead, row pointers
-// and aux values one step ahead, so a step's own latency is one round of
-// gathers, which the FMA chains of the SM's other warps cover.  The pass
-// starts from the pieces prefetched for it (if any) and ends by prefetching
-// the first pieces of the next pass (next_val of type Tn; nullptr for none).
-// Returns false (uniformly over the warp) if a wait gave up.
-template <typename T, typename X, typename Acc, typename Tn, typename Epi>
-__device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, const DevCsr& A, const T* val,
-                                          const X* x, const double* aux, Epi& epi, const Tn* next_val,
+// The product over the CTA's steps with values `val` (type T), gathering x;
+// consumer warp w computes steps s0 + w, s0 + w + kConsumerWarps, ...  Each
+// row's result goes to epi(i, yi, aux[i]) from one lane (aux[i] = 0 when aux
+// is nullptr).  kRingPass: entries come from the ring (the producer streams
+// them; the warp waits on the full barrier of the pieces a step spans and
+// releases pieces on the empty barriers once its next step starts beyond
+// them); otherwise entries are read directly from global memory (values
+// `val`, column indices A.col_idx).  Step descriptors are loaded two steps
+// ahead, row pointers and aux values one step ahead.  Returns false
+// (uniformly over the warp) if a wait gave up.
+template <bool kRingPass, typename T, typename X, typename Acc, typename Epi>
+__device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& cs, ConsumerCursor& cur,
+                                          const DevCsr& A, const T* val, const X* x, const double* aux, Epi& epi,
                                           unsigned long long limit_ns) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* rv = sm.val<T>(w);
-  const int32_t* rc = sm.col(w);
+  const T* rv = kRingPass ? sm.val<T>() : val;
+  const int32_t* rc = kRingPass ? sm.col() : A.col_idx;
   const int32_t* row_ptr = A.row_ptr;
-  if (!stream_begin_pass<T>(sm, ws, val, A.col_idx, limit_ns)) return false;
-  const int off = static_cast<int>((ws.gbase % kSlots) * kPiece) - ws.kb;  // ring pos = (k + off) & mask
-  // descriptor index clamped to the array (two sentinels follow the last step)
-  auto sd = [&](int k) { return k < A.nsteps + 2 ? k : A.nsteps + 1; };
+  const uint32_t gbase = cur.gbase;
+  // entry k sits at rv[pos(k)]: in the ring at (k + off) & kRingMask
+  const int off = static_cast<int>((gbase % kSlots) * kPiece) - cs.kb;
+  auto pos = [&](int k) { return kRingPass ? ((k + off) & kRingMask) : k; };
+  auto wait_piece = [&](int j) {
+    const uint32_t g = gbase + static_cast<uint32_t>(j);
+    return __all_sync(0xffffffffu, mbar_wait_bounded(sm.full(g % kSlots), (g / kSlots) & 1u, limit_ns, nullptr));
+  };
+  int released = 0;  // pieces of this pass this warp has released
+  auto release_upto = [&](int upto) -> bool {
+    for (; released < upto; ++released) {
+      if (!wait_piece(released)) return false;  // the piece must be the slot's current one
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sm.empty((gbase + static_cast<uint32_t>(released)) % kSlots));
+    }
+    return true;
+  };
+  auto sd = [&](int k) { return k < A.nsteps + 2 ? k : A.nsteps + 1; };  // two sentinels follow the last step
   auto holds_result = [&](int mode, const LaneRaw& r) {
     return r.row >= 0 && (mode == kLanePerRow || (lane & 1) == 0);
   };
+  constexpr int kStride = kConsumerWarps;
   Acc seg_acc = Acc(0);
-  int s = ws.s0;
-  int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + 1)];
-  int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + 1)];
-  LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < ws.s1);
-  double a0 = (aux != nullptr && s < ws.s1 && holds_result(m0 & 3, r0)) ? aux[r0.row] : 0.0;
-  for (; s < ws.s1; ++s) {
-    const bool has1 = s + 1 < ws.s1;
-    // prefetch: descriptor of step s+2, row pointers and aux value of step s+1
-    const int4 d2 = A.step[sd(s + 2)];
-    const int m2 = A.step_mode[sd(s + 2)];
+  int s = cs.s0 + w;
+  int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + kStride)];
+  int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + kStride)];
+  LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < cs.s1);
+  double a0 = (aux != nullptr && s < cs.s1 && holds_result(m0 & 3, r0)) ? aux[r0.row] : 0.0;
+  for (; s < cs.s1; s += kStride) {
+    const bool has1 = s + kStride < cs.s1;
+    // prefetch: descriptor two steps ahead, row pointers and aux value of the next step
+    const int4 d2 = A.step[sd(s + 2 * kStride)];
+    const int m2 = A.step_mode[sd(s + 2 * kStride)];
     const LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, has1);
     const double a1 = (aux != nullptr && has1 && holds_result(m1 & 3, r1)) ? aux[r1.row] : 0.0;
-    // this step's entries must be in the ring
-    if (d0.w > d0.z && !stream_wait_upto(sm, ws, ((d0.w - 1 - ws.kb) >> kPieceLog) + 1, limit_ns)) return false;
+    if (kRingPass && d0.w > d0.z) {
+      // release what lies before this step, then wait for the pieces it spans
+      if (!release_upto((d0.z - cs.kb) >> kPieceLog)) return false;
+      const int jh = (d0.w - 1 - cs.kb) >> kPieceLog;
+      for (int j = (d0.z - cs.kb) >> kPieceLog; j <= jh; ++j)
+        if (!wait_piece(j)) return false;
+    }
     const int mode = m0 & 3;
     if (mode == kSegment) {
       if (m0 & kSegFirst) seg_acc = Acc(0);
       for (int k = d0.z + lane; k < d0.w; k += 32) {
-        const int p = (k + off) & kRingMask;
+        const int p = pos(k);
         seg_acc = fma(Acc(rv[p]), Acc(x[rc[p]]), seg_acc);
       }
       if (m0 & kSegLast) {
@@ -579,7 +582,7 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
       const int wmax = (m0 >> kWmaxShift) & 0xff;
       int a, len;
       lane_span(r0, mode, a, len);
-      const int p0 = (a + off) & kRingMask;
+      const int p0 = pos(a);
       X xv[kLaneMax];
       seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
       const Acc part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv);
@@ -591,21 +594,13 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, WarpStream& ws, co
         epi(r0.row, part, a0);
       }
     }
-    // release the pieces that end before step s+1's first entry and refill
-    const int rel = has1 ? ((d1.z - ws.kb) >> kPieceLog) : ws.npieces;
-    if (rel > ws.released) {
-      __syncwarp();
-      while (rel > ws.released) {
-        const int upto = rel < ws.issued ? rel : ws.issued;
-        if (!stream_wait_upto(sm, ws, upto, limit_ns)) return false;  // a slot is refilled only once complete
-        ws.released = upto;
-        stream_fill<T>(sm, ws, val, A.col_idx);
-      }
-    }
     d0 = d1; m0 = m1; r0 = r1; a0 = a1;
     d1 = d2; m1 = m2;
   }
-  stream_end_pass<Tn>(sm, ws, next_val, A.col_idx);
+  if (kRingPass) {
+    if (!release_upto(cs.npieces)) return false;
+    cur.gbase = gbase + static_cast<uint32_t>(cs.npieces);
+  }
   return true;
 }
 

@@ -6,33 +6,36 @@
 
 namespace cgk {
 
-// The persistent kernels run one 256-thread CTA per SM.
-constexpr int kBlock = 256;
+// The persistent kernels run one CTA per SM: kConsumerWarps consumer warps
+// that compute, plus one producer warp that streams the CSR matrix into a
+// shared-memory ring with 1-D TMA bulk copies (warp specialisation).
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;  // 256 computing threads
+constexpr int kBlock = kConsumers + 32;          // + the producer warp
 constexpr int kCtasPerSm = 1;
-constexpr int kWarps = kBlock / 32;
+constexpr int kWarps = kConsumerWarps;           // warps taking part in CTA reductions
 
-// Matrix stream of a warp: each warp owns a contiguous run of rows and
-// streams their CSR values and column indices through a private
-// shared-memory ring of kSlots pieces of kPiece entries; a piece is one pair
-// of 1-D TMA bulk copies issued by the warp's lane 0 and completing on the
-// slot's mbarrier.  Warps never wait for each other inside the product.
-constexpr int kPieceLog = 9;
-constexpr int kPiece = 1 << kPieceLog;  // 512 entries
-constexpr int kSlots = 4;
-constexpr int kRing = kPiece * kSlots;  // 2048 entries per warp: 16 KB of FP64 values + 8 KB of indices
+// Matrix stream of a CTA: its CSR values and column indices, one pass after
+// another, flow through a ring of kSlots pieces of kPiece entries.  Each slot
+// has a "full" mbarrier (TMA completion) and an "empty" mbarrier on which
+// every consumer warp arrives once it no longer needs the piece.
+constexpr int kPieceLog = 11;
+constexpr int kPiece = 1 << kPieceLog;  // 2048 entries: 16 KB of FP64 values + 8 KB of indices
+constexpr int kSlots = 8;
+constexpr int kRing = kPiece * kSlots;  // 16384 entries
 constexpr int kRingMask = kRing - 1;
-// Entries mirrored behind the end of each ring: the head of the piece in
+// Entries mirrored behind the end of the ring: the head of the piece in
 // slot 0 is copied there as well, so a row segment of up to kMirror entries
 // starting anywhere in the ring reads contiguously, without wrapping.
 constexpr int kMirror = 32;
-// A step is what a warp computes at once: up to 32 rows of <= 32 entries
-// (one lane per row), up to 16 rows of 33..64 entries (two lanes per row), or
-// a segment of <= kSegNnz entries of one longer row (lanes stride the
-// segment; the row's sum is completed at its last segment).  A step holds at
-// most kStepNnz entries: half the ring, so later pieces stream in while it is
-// computed.
-constexpr int kStepNnz = kRing / 2;
-constexpr int kSegNnz = kPiece;
+// A step is what a consumer warp computes at once: up to 32 rows of <= 32
+// entries (one lane per row), up to 16 rows of 33..64 entries (two lanes per
+// row), or a segment of <= kSegNnz entries of one longer row (lanes stride the
+// segment; the row's sum is completed at its last segment).  Steps of a CTA
+// go to its consumer warps round-robin; a step holds at most kStepNnz entries
+// (so it spans at most two pieces).
+constexpr int kStepNnz = 1024;
+constexpr int kSegNnz = 512;
 constexpr int kLaneMax = 32;  // longest row computed by a single lane
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
@@ -58,7 +61,7 @@ struct DevCsr {
   const float* val32;         // [nnz + kPadEntries] FP32 copy (mixed precision) or nullptr
   const int4* step;           // [nsteps + 2] {r0, r1, e0, e1} (two trailing sentinels)
   const int32_t* step_mode;   // [nsteps + 2] StepMode | flags
-  const int32_t* warp_step;   // [nblocks * kWarps + 1] first step of each warp
+  const int32_t* block_step;  // [nblocks + 1] first step of each CTA
   const int32_t* block_row;   // [nblocks + 1] first row of each CTA (vector phases)
   int32_t n;
   int32_t nsteps;

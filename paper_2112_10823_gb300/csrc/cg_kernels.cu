@@ -26,16 +26,24 @@
 
 namespace cgk {
 
-// Leave the kernel after a failed wait: drain in-flight copies, record status.
-__device__ __forceinline__ void solve_fail(const RingSmem& sm, WarpStream& rs, const SolveParams& P) {
-  stream_drain(sm, rs, P.wait_limit_ns);
+// Consumers leaving the kernel: tell the producer to stop (it then waits for
+// its copies in flight and exits).
+__device__ __forceinline__ void consumers_done(const RingSmem& sm) {
+  cta_sync();
+  if (threadIdx.x == 0) *reinterpret_cast<volatile int32_t*>(sm.stop()) = 1;
+}
+
+// Leave the kernel after a failed wait: record the status, stop the producer.
+__device__ __forceinline__ void solve_fail(const RingSmem& sm, const SolveParams& P) {
   if (threadIdx.x == 0) {
     atomicExch(&P.ctrl->abort, 1);
     atomicExch(&P.ctrl->status, kETIMEOUT);
   }
+  __syncwarp();
+  if (threadIdx.x == 0) *reinterpret_cast<volatile int32_t*>(sm.stop()) = 1;
 }
 
-// CTA sums each thread reads in the grid-wide sum: nblocks <= kMaxCtaSums * kBlock.
+// CTA sums each thread reads in the grid-wide sum: nblocks <= kMaxCtaSums * kConsumers.
 constexpr int kMaxCtaSums = 4;
 
 template <bool kMixed>
@@ -45,8 +53,22 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   const DevCsr& A = P.A;
   const int bid = blockIdx.x;
   const int tid = threadIdx.x;
-  const int row0 = A.block_row[bid], row1 = A.block_row[bid + 1];
   const unsigned long long lim = P.wait_limit_ns;
+  CtaStream cs;
+  stream_setup(sm, cs, A);  // the last barrier of all threads
+  if (tid >= kConsumers) {  // the producer warp
+    if (tid == kConsumers) {
+      bool ok;
+      if constexpr (kMixed) ok = producer_loop<float>(sm, cs, A.val32, A.col_idx, -1, lim);
+      else ok = producer_loop<double>(sm, cs, A.val, A.col_idx, -1, lim);
+      if (!ok) {
+        atomicExch(&P.ctrl->abort, 1);
+        atomicExch(&P.ctrl->status, kETIMEOUT);
+      }
+    }
+    return;
+  }
+  const int row0 = A.block_row[bid], row1 = A.block_row[bid + 1];
   int32_t* flag = sm.flag();
   double* sc = sm.scalars();  // broadcast slots for per-step scalars
   FxScratch* fx = sm.fx();
@@ -58,12 +80,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   double* __restrict__ q = P.q;
   float* __restrict__ p32 = P.p32;
   const int nb = gridDim.x;
-  const double* const no_next = nullptr;
-  const float* const no_next32 = nullptr;
-  (void)no_next32;
-
-  WarpStream rs;
-  stream_init(sm, rs, A);
+  ConsumerCursor cur;
   GridBarrier gb;
   int slot = 0;
   int site = 0;
@@ -79,16 +96,25 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     double* part = P.partials + static_cast<size_t>(slot) * nb;
     if (tid == 0) part[bid] = cta;
     if (!gb.sync(ctrl, lim, ++site, flag)) return false;
-    // every CTA sums all nb CTA values (up to kMaxCtaSums per thread)
     double mine[kMaxCtaSums];
 #pragma unroll
     for (int j = 0; j < kMaxCtaSums; ++j) {
-      const int c = tid + j * kBlock;
+      const int c = tid + j * kConsumers;
       mine[j] = c < nb ? __ldcg(part + c) : 0.0;
     }
     out = fx_block_sum<kMaxCtaSums>(mine, fx);
     slot ^= 1;
     return true;
+  };
+  // FP64 products: from the ring in the FP64 solve; read directly from
+  // global memory in the mixed solve (whose ring carries the FP32 values).
+  // Every product pass ends with a vote of all consumer warps, so that a warp
+  // that gave up on a wait and the others leave together.
+  auto product64 = [&](const double* xin, const double* aux, auto& epi) -> bool {
+    bool ok;
+    if constexpr (kMixed) ok = spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
+    else ok = spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
+    return cta_and(ok);
   };
 
   // ---- setup: r = b - A x, p = r, rho = r.r, ||b||^2
@@ -102,16 +128,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       acc_rr = fma(ri, ri, acc_rr);
       acc_bb = fma(bi, bi, acc_bb);
     };
-    bool ok;
-    if constexpr (kMixed) ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val32, lim);
-    else ok = spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val, lim);
-    if (!ok) { solve_fail(sm, rs, P); return; }
+    if (!product64(x, b, epi)) { solve_fail(sm, P); return; }
   }
   double rho, bnorm2;
-  if (!allreduce(acc_rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, rs, P); return; }
+  if (!allreduce(acc_rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, P); return; }
   if (bnorm2 == 0.0) {  // b = 0: the solution is 0
-    stream_drain(sm, rs, lim);
-    for (int i = row0 + tid; i < row1; i += kBlock) x[i] = 0.0;
+    for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = 0.0;
     if (bid == 0 && tid == 0) {
       ctrl->status = kOK;
       ctrl->iters = 0;
@@ -120,6 +142,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       ctrl->relres_rec = 0.0;
       ctrl->relres_true = 0.0;
     }
+    consumers_done(sm);
     return;
   }
   // Stopping test sqrt(rho) <= tol ||b|| evaluated as rho <= tol^2 ||b||^2
@@ -139,37 +162,37 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
         q[i] = qi;
         acc_g = fma(pi, qi, acc_g);
       };
-      ok = spmv_pass<float, float, float>(sm, rs, A, A.val32, p32, p, epi, A.val32, lim);
+      ok = cta_and(spmv_pass<true, float, float, float>(sm, cs, cur, A, A.val32, p32, p, epi, lim));
     } else {
       auto epi = [&](int i, double s, double pi) {
         q[i] = s;
         acc_g = fma(pi, s, acc_g);
       };
-      ok = spmv_pass<double, double, double>(sm, rs, A, A.val, p, p, epi, A.val, lim);
+      ok = cta_and(spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, p, p, epi, lim));
     }
     double gamma;
-    if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, rs, P); return; }
+    if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, P); return; }
     if (!(gamma > 0.0) || !isfinite(gamma)) {  // not SPD, or overflow
       status = kEBREAKDOWN;
       break;
     }
     // alpha = rho / gamma, computed once and broadcast (FP64 division is slow)
     if (tid == 0) sc[0] = rho / gamma;
-    __syncthreads();
+    cta_sync();
     const double alpha = sc[0];
 
     // ---- r -= alpha q, rho' = r.r   (four rows per thread in flight)
     double acc_r = 0.0;
-    for (int base = row0 + tid; base < row1; base += 4 * kBlock) {
+    for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
       double qv[4], rv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int i = base + u * kBlock;
+        const int i = base + u * kConsumers;
         if (i < row1) { qv[u] = q[i]; rv[u] = r[i]; }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int i = base + u * kBlock;
+        const int i = base + u * kConsumers;
         if (i < row1) {
           const double rn = fma(-alpha, qv[u], rv[u]);
           r[i] = rn;
@@ -178,35 +201,31 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       }
     }
     double rho_new;
-    if (!allreduce(acc_r, rho_new)) { solve_fail(sm, rs, P); return; }
+    if (!allreduce(acc_r, rho_new)) { solve_fail(sm, P); return; }
     ++k;
 
     bool replace = false;
     if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rho_new <= thresh2;
     if (replace) {
       // x += alpha p, then r = b - A x in FP64 (residual replacement)
-      for (int i = row0 + tid; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
-      if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
+      for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
+      if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
       double acc_t = 0.0;
       auto epi = [&](int i, double s, double bi) {
         const double ri = bi - s;
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
       };
-      if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, A.val32, lim) ||
-          !allreduce(acc_t, rho_new)) {
-        solve_fail(sm, rs, P);
-        return;
-      }
+      if (!product64(x, b, epi) || !allreduce(acc_t, rho_new)) { solve_fail(sm, P); return; }
       if (rho_new <= thresh2) {
         rho = rho_new;
         done = true;
         break;
       }
       if (tid == 0) sc[1] = rho_new / rho;
-      __syncthreads();
+      cta_sync();
       const double beta = sc[1];
-      for (int i = row0 + tid; i < row1; i += kBlock) {
+      for (int i = row0 + tid; i < row1; i += kConsumers) {
         const double pi = fma(beta, p[i], r[i]);
         p[i] = pi;
         if constexpr (kMixed) p32[i] = static_cast<float>(pi);
@@ -214,25 +233,25 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       rho = rho_new;
     } else {
       if (!kMixed && rho_new <= thresh2) {
-        for (int i = row0 + tid; i < row1; i += kBlock) x[i] = fma(alpha, p[i], x[i]);
+        for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
         rho = rho_new;
         done = true;
         break;
       }
       // ---- x += alpha p; p = r + beta p
       if (tid == 0) sc[1] = rho_new / rho;
-      __syncthreads();
+      cta_sync();
       const double beta = sc[1];
-      for (int base = row0 + tid; base < row1; base += 4 * kBlock) {
+      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
         double pv[4], rv[4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = base + u * kBlock;
+          const int i = base + u * kConsumers;
           if (i < row1) { pv[u] = p[i]; rv[u] = r[i]; xv[u] = x[i]; }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = base + u * kBlock;
+          const int i = base + u * kConsumers;
           if (i < row1) {
             x[i] = fma(alpha, pv[u], xv[u]);
             const double pn = fma(beta, pv[u], rv[u]);
@@ -243,12 +262,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       }
       rho = rho_new;
     }
-    if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
+    if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
   }
   if (status == kOK && !done) status = kENOTCONV;
 
   // ---- true residual ||b - A x|| / ||b|| (x complete everywhere first)
-  if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, rs, P); return; }
+  if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
   double acc_t = 0.0;
   {
     auto epi = [&](int i, double s, double bi) {
@@ -256,11 +275,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
       acc_t = fma(d, d, acc_t);
     };
     double tsum;
-    if (!spmv_pass<double, double, double>(sm, rs, A, A.val, x, b, epi, no_next, lim) ||
-        !allreduce(acc_t, tsum)) {
-      solve_fail(sm, rs, P);
-      return;
-    }
+    if (!product64(x, b, epi) || !allreduce(acc_t, tsum)) { solve_fail(sm, P); return; }
     acc_t = tsum;
   }
   if (bid == 0 && tid == 0) {
@@ -271,21 +286,26 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     ctrl->relres_rec = sqrt(rho / bnorm2);
     ctrl->relres_true = sqrt(acc_t / bnorm2);
   }
+  consumers_done(sm);
 }
 
-// y = A x over the CTA's rows (same partition and streams as the solve).
+// y = A x (same partition and stream as the solve; one pass).
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A, const double* __restrict__ x,
                                                                    double* __restrict__ y, int32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
-  WarpStream ws;
-  stream_init(sm, ws, A);
-  auto epi = [&](int i, double s, double) { y[i] = s; };
-  const double* const no_next = nullptr;
-  if (!spmv_pass<double, double, double>(sm, ws, A, A.val, x, nullptr, epi, no_next, 2000000000ull)) {
-    stream_drain(sm, ws, 2000000000ull);
-    if ((threadIdx.x & 31) == 0) atomicExch(err, kETIMEOUT);
+  CtaStream cs;
+  stream_setup(sm, cs, A);
+  const unsigned long long lim = 2000000000ull;
+  if (threadIdx.x >= kConsumers) {
+    if (threadIdx.x == kConsumers && !producer_loop<double>(sm, cs, A.val, A.col_idx, 1, lim)) atomicExch(err, kETIMEOUT);
+    return;
   }
+  ConsumerCursor cur;
+  auto epi = [&](int i, double s, double) { y[i] = s; };
+  const bool ok = cta_and(spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, x, nullptr, epi, lim));
+  if (!ok && threadIdx.x == 0) atomicExch(err, kETIMEOUT);
+  consumers_done(sm);
 }
 
 namespace {
@@ -342,9 +362,10 @@ cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
                                      dim3(kBlock), args, RingSmem::kBytes, s);
 }
 
-// ---- self-test of the bounded wait: one CTA waits at a grid barrier that
-// expects one more arrival than the grid can give, so the wait must run out
-// after limit_ns and report kETIMEOUT through the control block.
+// ---- self-test of the bounded wait: one CTA (of kConsumers threads, the
+// grid barrier's CTA size) waits at a grid barrier that expects one more
+// arrival than the grid can give, so the wait must run out after limit_ns and
+// report kETIMEOUT through the control block.
 __global__ void wait_timeout_selftest_kernel(SolveCtrl* ctrl, unsigned long long limit_ns) {
   __shared__ int32_t flag;
   GridBarrier gb;
@@ -357,7 +378,7 @@ __global__ void wait_timeout_selftest_kernel(SolveCtrl* ctrl, unsigned long long
 }
 
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s) {
-  wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(ctrl, limit_ns);
+  wait_timeout_selftest_kernel<<<1, kConsumers, 0, s>>>(ctrl, limit_ns);
   return cudaGetLastError();
 }
 
