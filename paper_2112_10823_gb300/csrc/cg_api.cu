@@ -102,10 +102,10 @@ bool is_device_ptr(const void* p) {
 // Row partition of the persistent kernels.  Rows are split into `nblocks`
 // contiguous CTA ranges of about equal cost (stored entries + kRowCost per
 // row, the per-row vector work), and each CTA range into steps (see
-// cg_internal.h): up to 32 rows
-// of <= 16 entries, up to 16 rows of <= 64 entries, or segments of <= kSegNnz
-// entries of a longer row, never more than kStepNnz entries per step.  Two
-// sentinel steps follow the last one (the kernels read descriptors ahead).
+// cg_internal.h): up to 32 rows of <= 32 entries (one lane per row), up to 16
+// rows of <= 64 entries (two lanes per row), never more than kStepNnz entries,
+// or one longer row.  Two sentinel steps follow the last one (the kernels
+// read descriptors ahead).
 constexpr int64_t kRowCost = 6;
 
 struct Partition {
@@ -133,16 +133,9 @@ void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partit
   const int64_t kPairMax = 2 * cgk::kLaneMax;
   while (row < end) {
     const int64_t len0 = rp[row + 1] - rp[row];
-    if (len0 > kPairMax) {  // a long row: segments through the ring
-      for (int64_t e = rp[row]; e < rp[row + 1]; e += cgk::kSegNnz) {
-        const int64_t e1 = std::min<int64_t>(e + cgk::kSegNnz, rp[row + 1]);
-        int32_t m = cgk::kSegment;
-        if (e == rp[row]) m |= cgk::kSegFirst;
-        if (e1 == rp[row + 1]) m |= cgk::kSegLast;
-        P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), static_cast<int>(e),
-                                   static_cast<int>(e1)));
-        P.step_mode.push_back(m);
-      }
+    if (len0 > kPairMax) {  // a long row: one step, walked piece by piece
+      P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), rp[row], rp[row + 1]));
+      P.step_mode.push_back(cgk::kLongRow);
       ++row;
       continue;
     }

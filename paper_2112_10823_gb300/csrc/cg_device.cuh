@@ -478,7 +478,7 @@ struct LaneRaw {
 __device__ __forceinline__ LaneRaw lane_raw(const int32_t* row_ptr, int4 d, int mode, bool valid) {
   const int lane = threadIdx.x & 31;
   LaneRaw r{-1, 0, 0};
-  if (valid && mode != kSegment) {
+  if (valid && mode != kLongRow) {
     const int i = d.x + (mode == kLanePerRow ? lane : (lane >> 1));
     if (i < d.y) {
       r.row = i;
@@ -545,7 +545,6 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
     return r.row >= 0 && (mode == kLanePerRow || (lane & 1) == 0);
   };
   constexpr int kStride = kConsumerWarps;
-  Acc seg_acc = Acc(0);
   int s = cs.s0 + w;
   int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + kStride)];
   int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + kStride)];
@@ -558,26 +557,39 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
     const int m2 = A.step_mode[sd(s + 2 * kStride)];
     const LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, has1);
     const double a1 = (aux != nullptr && has1 && holds_result(m1 & 3, r1)) ? aux[r1.row] : 0.0;
-    if (kRingPass && d0.w > d0.z) {
-      // release what lies before this step, then wait for the pieces it spans
-      if (!release_upto((d0.z - cs.kb) >> kPieceLog)) return false;
-      const int jh = (d0.w - 1 - cs.kb) >> kPieceLog;
-      for (int j = (d0.z - cs.kb) >> kPieceLog; j <= jh; ++j)
-        if (!wait_piece(j)) return false;
-    }
     const int mode = m0 & 3;
-    if (mode == kSegment) {
-      if (m0 & kSegFirst) seg_acc = Acc(0);
-      for (int k = d0.z + lane; k < d0.w; k += 32) {
-        const int p = pos(k);
-        seg_acc = fma(Acc(rv[p]), Acc(x[rc[p]]), seg_acc);
+    if (kRingPass && d0.w > d0.z) {
+      // release what lies before this step; a short step then waits for the
+      // (at most two) pieces it spans
+      if (!release_upto((d0.z - cs.kb) >> kPieceLog)) return false;
+      if (mode != kLongRow) {
+        const int jh = (d0.w - 1 - cs.kb) >> kPieceLog;
+        for (int j = (d0.z - cs.kb) >> kPieceLog; j <= jh; ++j)
+          if (!wait_piece(j)) return false;
       }
-      if (m0 & kSegLast) {
-        Acc tot;
-        if constexpr (sizeof(Acc) == 8) tot = warp_sum(seg_acc);
-        else tot = warp_sum_f(seg_acc);
-        if (lane == 0) epi(d0.x, tot, aux != nullptr ? aux[d0.x] : 0.0);
+    }
+    if (mode == kLongRow) {
+      // lanes stride the row; in a ring pass piece by piece, each piece
+      // released once done (the warp's next step starts after this row)
+      Acc acc = Acc(0);
+      if (kRingPass) {
+        const int jl = (d0.z - cs.kb) >> kPieceLog, jh = (d0.w - 1 - cs.kb) >> kPieceLog;
+        for (int j = jl; j <= jh; ++j) {
+          if (!wait_piece(j)) return false;
+          const int lo = max(d0.z, cs.kb + j * kPiece), hi = min(d0.w, cs.kb + (j + 1) * kPiece);
+          for (int k = lo + lane; k < hi; k += 32) {
+            const int p = pos(k);
+            acc = fma(Acc(rv[p]), Acc(x[rc[p]]), acc);
+          }
+          if (j < jh && !release_upto(j + 1)) return false;
+        }
+      } else {
+        for (int k = d0.z + lane; k < d0.w; k += 32) acc = fma(Acc(rv[k]), Acc(x[rc[k]]), acc);
       }
+      Acc tot;
+      if constexpr (sizeof(Acc) == 8) tot = warp_sum(acc);
+      else tot = warp_sum_f(acc);
+      if (lane == 0) epi(d0.x, tot, aux != nullptr ? aux[d0.x] : 0.0);
     } else {
       const int wmax = (m0 >> kWmaxShift) & 0xff;
       int a, len;

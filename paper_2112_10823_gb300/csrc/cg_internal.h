@@ -30,12 +30,11 @@ constexpr int kRingMask = kRing - 1;
 constexpr int kMirror = 32;
 // A step is what a consumer warp computes at once: up to 32 rows of <= 32
 // entries (one lane per row), up to 16 rows of 33..64 entries (two lanes per
-// row), or a segment of <= kSegNnz entries of one longer row (lanes stride the
-// segment; the row's sum is completed at its last segment).  Steps of a CTA
-// go to its consumer warps round-robin; a step holds at most kStepNnz entries
-// (so it spans at most two pieces).
+// row), both at most kStepNnz entries (so they span at most two pieces), or
+// one longer row, whose entries the warp walks piece by piece (lanes stride
+// them), releasing each piece as soon as it is done with it, so a row may be
+// longer than the ring.  Steps of a CTA go to its consumer warps round-robin.
 constexpr int kStepNnz = 1024;
-constexpr int kSegNnz = 512;
 constexpr int kLaneMax = 32;  // longest row computed by a single lane
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
@@ -44,11 +43,8 @@ constexpr int kPadEntries = 8;
 enum StepMode : int32_t {
   kLanePerRow = 0,   // lane l computes row r0 + l (rows of <= kLaneMax entries)
   kPairPerRow = 1,   // lanes 2t, 2t+1 split row r0 + t (rows of <= 2 kLaneMax entries)
-  kSegment = 2,      // entries [e0, e1) of row r0; lanes stride them
+  kLongRow = 2,      // the whole row r0 (entries [e0, e1)); lanes stride it
 };
-// Flags of a kSegment step (stored above the mode bits).
-constexpr int32_t kSegFirst = 4;
-constexpr int32_t kSegLast = 8;
 // Bits 8..15 of a step's mode word: the longest per-lane segment of the step
 // (precomputed so that the lanes need no warp reduction to bound their loops).
 constexpr int kWmaxShift = 8;
