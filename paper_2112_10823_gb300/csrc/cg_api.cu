@@ -322,7 +322,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     return rc;
   }
   h->nblocks = sms * per_sm;
-  if (h->nblocks > 4 * cgk::kBlock) {  // the grid-wide sum reads at most 4 CTA sums per thread
+  if (h->nblocks > 2 * cgk::kConsumers) {  // the grid-wide sum reads at most 2 CTA sums per thread
     int rc = fail(nullptr, CG_ECUDA, "cg_create: more persistent CTAs than the grid-wide sum supports");
     release(h);
     delete h;

@@ -44,7 +44,7 @@ __device__ __forceinline__ void solve_fail(const RingSmem& sm, const SolveParams
 }
 
 // CTA sums each thread reads in the grid-wide sum: nblocks <= kMaxCtaSums * kConsumers.
-constexpr int kMaxCtaSums = 4;
+constexpr int kMaxCtaSums = 2;
 
 template <bool kMixed>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
