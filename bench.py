@@ -240,6 +240,26 @@ def dist_setup(args):
     return world, rank, local
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of the system a rank solves: every replica gets its own system."""
+    return seed + rank
+
+
+def max_over_ranks(t: float, pg, device) -> float:
+    """The slowest rank's time (the whole job ends when it ends)."""
+    if pg is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(steps: int, world: int, t_max: float) -> float:
+    """Solves per second of the whole job: all ranks' solves over the slowest rank's time."""
+    return steps * world / t_max
+
+
 def run_reference(args):
     """The oracle (plain FP64 sequential C) on the same workload, host cores."""
     world, rank, local = dist_setup(args)
@@ -299,7 +319,7 @@ def run_ours(args):
         pg = dist
     import paper_2112_10823_gb300 as cg
 
-    seed = args.seed + rank
+    seed = replica_seed(args.seed, rank)
     A, xs = make_problem(seed, args.grid)
     n, nnz = A.n, A.nnz
     stream = torch.cuda.current_stream(dev)
@@ -343,12 +363,8 @@ def run_ours(args):
     solve_ms = [s.elapsed_time(e) for s, e in ev]
     dev_time = sum(solve_ms) / 1000.0
     assert res.status == cg.CG_OK and res.relres <= TOL, res
-    t_max = dev_time
-    if pg:
-        tt = torch.tensor([dev_time], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = args.steps * world / t_max
+    t_max = max_over_ranks(dev_time, pg, dev)
+    value = whole_job_rate(args.steps, world, t_max)
 
     # ---- end to end through the C ABI with pinned host buffers
     b_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -365,11 +381,8 @@ def run_ours(args):
         r2 = cg.cg_solve(h, b_host, x_host, tol=TOL, maxit=10 * n)
     t_e2e = time.perf_counter() - t0
     assert r2.status == cg.CG_OK
-    if pg:
-        tt = torch.tensor([t_e2e], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": args.steps * world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
+    t_e2e = max_over_ranks(t_e2e, pg, dev)
+    e2e = {"value": whole_job_rate(args.steps, world, t_e2e), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
            "d2h_bytes_per_step": 8 * n}
 
     # ---- latency percentiles and board energy over back-to-back solves
