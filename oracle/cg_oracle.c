@@ -166,8 +166,13 @@ void oracle_spmv_f32(int64_t n, const int32_t* IA, const int32_t* JA, const floa
  *   Every step:  p32 = (float)p;  q = (double)(A32 p32)  [FP32 product, FP32 sums]
  *                gamma = p.q, alpha, x, r, rho_new, beta, p all in FP64 as in oracle_cg.
  *   Every `replace_every` steps (and before declaring convergence), r is
- *   replaced by the true FP64 residual b - A x (product with AA), rho is
- *   recomputed from it, and the step continues from that r (p is kept).
+ *   replaced by the true FP64 residual b - A x (product with AA) and rho is
+ *   recomputed from it; the direction update keeps the recurrence's own
+ *   ratio, beta = rho_rec / rho with rho_rec the recursive r.r of this step,
+ *   so p = r_true + beta p.  (With beta = rho_true / rho instead, a system
+ *   whose recursive residual reaches tol long before the true one does gets
+ *   beta >> 1 at that replacement and the iteration stalls along the old
+ *   direction: the small Q1 systems never converge that way.)
  *   Convergence needs the true residual: sqrt(rho_true) <= tol*||b||.
  * Returns iterations and both residual measures as oracle_cg does.
  */
@@ -206,6 +211,7 @@ int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const doubl
         for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
         for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
         double rho_new = oracle_dot(n, r, r);
+        double beta = rho_new / rho;
         k = k + 1;
         int replace = (replace_every > 0 && k % replace_every == 0) || sqrt(rho_new) <= tol * bnorm;
         if (replace) {
@@ -214,7 +220,6 @@ int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const doubl
             rho_new = oracle_dot(n, r, r);
             if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }
         }
-        double beta = rho_new / rho;
         for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
         rho = rho_new;
     }

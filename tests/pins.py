@@ -232,6 +232,19 @@ def pin_mixed_cg():
     y32 = oracle.spmv_f32(A, v32, x32).astype(np.float64)
     ref = np.abs(D) @ np.abs(xs)
     assert np.all(np.abs(y32 - D @ xs) <= 40 * 2.0 ** -24 * ref)
+    # Systems whose recursive residual reaches the tolerance before the first
+    # periodic replacement (the FP32 product has drifted it away from the true
+    # one by then): mixed precision must still reach the FP64 true residual,
+    # within a few steps of what FP64 CG needs (a refinement step costs a few).
+    for N, seed in ((4, 1), (6, 906), (10, 910)):
+        A = fi.q1(N, sigma=1.0, seed=seed)
+        D = A.to_dense()
+        b = D @ fi.xstar(seed, A.n)
+        r = oracle.cg_mixed(A, b, tol=1e-10, replace_every=50)
+        r64 = oracle.cg(A, b, tol=1e-10, maxit=10 * A.n)
+        assert r.status == oracle.OK, (N, r.status, r.iters)
+        assert np.linalg.norm(b - D @ r.x) <= 1e-10 * np.linalg.norm(b) * 1.0000001
+        assert r.iters <= 1.5 * r64.iters + 10, (N, r.iters, r64.iters)
 
 
 def pin_matrix_stats(golden_table1=True):

@@ -36,6 +36,9 @@ MUTANTS = [
      "if (force_iters < 0 && rho_new <= tol * bnorm)"),
     ("mixed_never_replaces", "int replace = (replace_every > 0 && k % replace_every == 0) || sqrt(rho_new) <= tol * bnorm;",
      "int replace = 0; if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }"),
+    ("mixed_beta_from_true_residual",
+     "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
+     "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n            beta = rho_new / rho;\n        }"),
     ("stats_bandwidth_off_by_one", "int64_t d = (int64_t)(JA[k] - base) - i;", "int64_t d = (int64_t)(JA[k] - base) - i + 1;"),
 ]
 
