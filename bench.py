@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("CG solves/s and SpMV HBM GB/s (% of roofline), joules/solve, p50/p99 latency at rel-res 1e-10")
 GRID_N = 64
+# Steps of an FP64 solve per grid edge on these systems (396 at 64^3), used
+# only to size the oracle's sample on systems too large to solve on the host.
+ITERS_PER_EDGE = 6.2
 SIGMA = 1.0
 TOL = 1e-10
 L2_FLUSH_BYTES = 256 << 20  # > the 126.5 MiB L2
@@ -48,7 +51,7 @@ L2_FLUSH_BYTES = 256 << 20  # > the 126.5 MiB L2
 FP64_PEAK_GFLOPS = 1201.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -58,8 +61,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-solves", type=int, default=200)
     ap.add_argument("--grid", type=int, default=GRID_N,
-                    help="grid edge of the Q1 system (64 is the benchmark workload; others for profiling)")
-    return ap.parse_args()
+                    help="grid edge of the Q1 system (64 is the benchmark workload; 160 the large system)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: the paper's FP64 CG; mixed: FP32 product with FP64 residual replacement")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: one system per step (default); batch: 256 uneven systems per step; "
+                         "serve: Poisson request stream")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the arrival window")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="device memory budget of the server")
+    ap.add_argument("--chunk", type=int, default=50, help="serve: steps per system per round")
+    ap.add_argument("--cpu-budget", type=float, default=10.0,
+                    help="seconds of oracle work for cpu_baseline (and per reference-arm step on large systems)")
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -82,6 +97,45 @@ def algorithmic_bytes_per_iter(n: int, nnz: int) -> int:
 
 def flops_per_iter(n: int, nnz: int) -> int:
     return 2 * nnz + 10 * n
+
+
+def mixed_bytes_per_iter(n: int, nnz: int) -> int:
+    """One mixed-precision CG step: FP32 values and column indices (8 B per
+    entry), row pointers, and 96 B per row (p32 gather 4, p read 8 and q
+    write 8 for the FP64 p.q; x, r read+write 32 and p, q read 16; r read 8,
+    p read+write 16, p32 write 4)."""
+    return 8 * nnz + 4 * (n + 1) + 96 * n
+
+
+def replacement_bytes(n: int, nnz: int) -> int:
+    """One FP64 residual replacement r = b - A x: the FP64 product (12 B per
+    entry, row pointers, x gather 8) plus b read 8 and r write 8 per row."""
+    return 12 * nnz + 4 * (n + 1) + 24 * n
+
+
+def replacements(iters: int, every: int) -> int:
+    """Replacements of a mixed solve of `iters` steps: one every `every` steps
+    and one before convergence is accepted."""
+    return iters // every + 1
+
+
+def solve_bytes(n: int, nnz: int, iters: int, mixed: bool, every: int = 50) -> int:
+    if not mixed:
+        return iters * algorithmic_bytes_per_iter(n, nnz)
+    return iters * mixed_bytes_per_iter(n, nnz) + replacements(iters, every) * replacement_bytes(n, nnz)
+
+
+def solve_flops(n: int, nnz: int, iters: int, mixed: bool, every: int = 50) -> int:
+    f = iters * flops_per_iter(n, nnz)
+    if mixed:
+        f += replacements(iters, every) * (2 * nnz + 2 * n)
+    return f
+
+
+def l2_resident(n: int, nnz: int, mixed: bool) -> bool:
+    """Whether the matrix and the vectors of a solve fit in the 126.5 MiB L2."""
+    mat = (8 if mixed else 12) * nnz + 4 * (n + 1)
+    return mat + 48 * n < 100 * 2**20
 
 
 def spmv_bytes(n: int, nnz: int) -> int:
@@ -260,51 +314,88 @@ def whole_job_rate(steps: int, world: int, t_max: float) -> float:
     return steps * world / t_max
 
 
+def workload_name(grid: int, precision: str) -> str:
+    prec = "FP64 CSR" if precision == "fp64" else "FP32-value product with FP64 residual replacement every 50 steps"
+    return f"Q1 27-point FE, {grid}^3 grid, lognormal rho (sigma=1), {prec}, CG to 1e-10"
+
+
+def oracle_solver(precision: str):
+    import oracle
+    if precision == "mixed":
+        return lambda A, b, maxit: oracle.cg_mixed(A, b, tol=TOL, maxit=maxit)
+    return lambda A, b, maxit: oracle.cg(A, b, tol=TOL, maxit=maxit)
+
+
+def oracle_rate(A, b, precision: str, budget_s: float, iters_full: int):
+    """The oracle's solves/s on one host core: whole solves when one takes
+    less than half the budget, else runs of 20 steps (each with its setup
+    product) whose time per step is scaled to an `iters_full`-step solve.
+    Returns (solves/s, description of the sample)."""
+    solve = oracle_solver(precision)
+    m = 20
+    t0 = time.perf_counter()
+    solve(A, b, m)
+    per_step = (time.perf_counter() - t0) / (m + 1)
+    if per_step * (iters_full + 1) <= budget_s / 2:
+        n_done, t_tot = 0, 0.0
+        while n_done == 0 or t_tot < budget_s:
+            t0 = time.perf_counter()
+            r = solve(A, b, 10 * A.n)
+            t_tot += time.perf_counter() - t0
+            n_done += 1
+        return n_done / t_tot, (f"{n_done} complete oracle solves ({r.iters} iterations each), "
+                                f"single thread, {t_tot:.1f} s")
+    runs, t_tot = 0, 0.0
+    while runs == 0 or t_tot < budget_s:
+        t0 = time.perf_counter()
+        solve(A, b, m)
+        t_tot += time.perf_counter() - t0
+        runs += 1
+    per_step = t_tot / (runs * (m + 1))
+    return 1.0 / (per_step * (iters_full + 1)), (
+        f"{runs} oracle runs of {m} steps each plus the setup product (single thread, {t_tot:.1f} s), "
+        f"time per step scaled to a {iters_full}-step solve")
+
+
 def run_reference(args):
-    """The oracle (plain FP64 sequential C) on the same workload, host cores."""
+    """The oracle (plain sequential C, the paper's method as stated) on the same
+    workload, on the host cores."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return
     import oracle
     A, xs = make_problem(args.seed, args.grid)
     b = oracle.spmv(A, xs)
-    times, iters = [], 0
+    times, iters, sample = [], 0, ""
+    # a full solve per step where it takes seconds; a bounded sample otherwise
+    iters_hint = None if args.grid <= GRID_N else int(round(ITERS_PER_EDGE * args.grid))
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = oracle.cg(A, b, tol=TOL, maxit=10 * A.n)
-        dt = time.perf_counter() - t0
+        if iters_hint is None:
+            t0 = time.perf_counter()
+            r = oracle_solver(args.precision)(A, b, 10 * A.n)
+            dt = time.perf_counter() - t0
+            iters = r.iters
+            sample = f"{args.steps} full oracle solves of the workload (each step one solve, {iters} iterations)"
+        else:
+            iters = iters_hint
+            v, sample = oracle_rate(A, b, args.precision, args.cpu_budget / 4, iters_hint)
+            dt = 1.0 / v
+            sample = "each step: " + sample
         if s >= args.warmup:
             times.append(dt)
-        iters = r.iters
     tot = sum(times)
     value = len(times) / tot
-    sample = f"{len(times)} full oracle solves of the workload (each step one solve, {iters} iterations)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"Q1 27-point FE, {args.grid}^3 grid, lognormal rho (sigma=1), FP64 CSR, CG to 1e-10",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.grid, args.precision),
                    "n": A.n, "nnz": A.nnz, "iters": iters, "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(A, xs, budget_s: float = 10.0):
-    import oracle
-    b = oracle.spmv(A, xs)
-    n_done, t_tot, iters = 0, 0.0, 0
-    while n_done == 0 or t_tot < budget_s:
-        t0 = time.perf_counter()
-        r = oracle.cg(A, b, tol=TOL, maxit=10 * A.n)
-        t_tot += time.perf_counter() - t0
-        n_done += 1
-        iters = r.iters
-    return {"value": n_done / t_tot, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_done} complete FP64 oracle solves of the same workload ({iters} iterations each), "
-                      f"single thread, {t_tot:.1f} s"}
 
 
 def run_ours(args):
@@ -326,7 +417,9 @@ def run_ours(args):
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col_idx).to(dev)
     va = torch.from_numpy(A.val).to(dev)
-    h = cg.cg_create(rp, ci, va, stream=stream)
+    mixed = args.precision == "mixed"
+    h = cg.cg_create(rp, ci, va, stream=stream, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64)
+    h64 = cg.cg_create(rp, ci, va, stream=stream) if mixed else None   # FP64 solve for the accuracy record
     del rp, ci, va
     xs_d = torch.from_numpy(xs).to(dev)
     b = torch.empty_like(xs_d)
@@ -420,34 +513,59 @@ def run_ours(args):
     hbm_peak, peak_kind = peaks()
     spmv_gbs = spmv_bytes(n, nnz) / (spmv_ms * 1e-3) / 1e9
 
+    # ---- accuracy of the timed solve: against x* and (mixed) the FP64 solve
+    x_fin = x.clone()
+    accuracy = {"relres_true": res.relres, "err_vs_xstar": float(torch.linalg.vector_norm(x_fin - xs_d)
+                                                                  / torch.linalg.vector_norm(xs_d))}
+    if mixed:
+        x64 = torch.zeros_like(b)
+        r64 = cg.cg_solve(h64, b, x64, tol=TOL, maxit=10 * n)
+        accuracy.update({"fp64_iters": r64.iters, "fp64_relres_true": r64.relres,
+                         "rel_diff_vs_fp64_solve": float(torch.linalg.vector_norm(x_fin - x64)
+                                                         / torch.linalg.vector_norm(x64))})
+        h64.close()
+
     # ---- roofline of the solve kernel (one launch per solve)
     launch_s = dev_time / args.steps
-    bytes_launch = iters * algorithmic_bytes_per_iter(n, nnz)
-    flops_launch = iters * flops_per_iter(n, nnz)
+    bytes_launch = solve_bytes(n, nnz, iters, mixed)
+    flops_launch = solve_flops(n, nnz, iters, mixed)
     achieved_gbs = bytes_launch / launch_s / 1e9
-    traffic = recorded_traffic("cg_solve_kernel<false>", f"q1_{args.grid}")
+    achieved_gflops = flops_launch / launch_s / 1e9
+    kname = f"cg_solve_kernel<{'true' if mixed else 'false'}>"
+    traffic = recorded_traffic(kname, f"q1_{args.grid}")
+    if l2_resident(n, nnz, mixed) or not mixed and achieved_gflops / FP64_PEAK_GFLOPS > achieved_gbs / hbm_peak:
+        # the system stays in L2 during a solve (or the FP64 pipe is nearer its
+        # peak than HBM is): the FP64 pipe bounds the kernel
+        roof = {"bound": "alu", "achieved": achieved_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved_gflops / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "peak_source": "measured (FP64 FMA probe)", "kernel": kname, "algorithmic_gbs": achieved_gbs,
+                "algorithmic_gbs_frac_of_hbm": achieved_gbs / hbm_peak, "hbm_peak_source": peak_kind}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": kname, "gflops": achieved_gflops, "gflops_frac_of_fp64": achieved_gflops / FP64_PEAK_GFLOPS}
 
     if rank != 0:
         if pg:
             pg.destroy_process_group()
         return
-    base = None if args.no_cpu_baseline else cpu_baseline(A, xs)
+    base = None
+    if not args.no_cpu_baseline:
+        import oracle
+        b_host = b.cpu().numpy()
+        v, sample = oracle_rate(A, b_host, args.precision, args.cpu_budget, iters)
+        base = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"Q1 27-point FE, {args.grid}^3 grid, lognormal rho (sigma=1), FP64 CSR, CG to 1e-10",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.grid, args.precision),
                    "n": n, "nnz": nnz, "iters": iters, "tol": TOL, "x0": "zero",
                    "l2": "flushed before every timed solve (256 MiB write)", "parallelism": f"replicas x{world}"},
-        # The 64^3 system stays in L2 during a solve (DRAM traffic is ~2 % of the
-        # algorithmic bytes), so its kernel is bound by the FP64 pipe, not HBM.
-        "roofline": {"bound": "alu", "achieved": flops_launch / launch_s / 1e9, "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": flops_launch / launch_s / 1e9 / FP64_PEAK_GFLOPS,
-                     "traffic": traffic, "peak_source": "measured (FP64 FMA probe)",
-                     "kernel": "cg_solve_kernel<false>", "algorithmic_gbs": achieved_gbs,
-                     "algorithmic_gbs_frac_of_hbm": achieved_gbs / hbm_peak, "hbm_peak_source": peak_kind},
+        "roofline": roof,
+        "accuracy": accuracy,
         "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm_peak, "ms": spmv_ms, "bytes": spmv_bytes(n, nnz),
-                 "l2": "flushed before every call"},
+                 "l2": "flushed before every call", "precision": "fp64"},
         "energy": {"joules_per_solve": joules, "avg_watts": watts, "source": "NVML board energy",
                    "solves": args.latency_solves},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -465,10 +583,297 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+# ----------------------------------------------------- batched and served
+
+def _upload(A, dev):
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(A.row_ptr, dtype=np.int32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(A.col_idx, dtype=np.int32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(A.val, dtype=np.float64)).to(dev))
+
+
+def _batch_systems(seed: int, count: int, dev):
+    """The uneven batch: edges uniform on {8..48}, own densities and
+    manufactured solution per system; matrices and right-hand sides resident
+    on the device, with an FP64 handle each (b = A x* on the device)."""
+    import torch
+    import fe_inputs as fi
+    import paper_2112_10823_gb300 as cg
+    out = []
+    for i, N in enumerate(fi.batch_edges(seed, count)):
+        sd = fi.system_seed(seed, i)
+        A = fi.q1(int(N), SIGMA, sd)
+        rp, ci, va = _upload(A, dev)
+        h = cg.cg_create(rp, ci, va)
+        xs = torch.from_numpy(fi.xstar(sd, A.n)).to(dev)
+        b = torch.empty_like(xs)
+        cg.cg_spmv(h, xs, b)
+        out.append({"N": int(N), "n": A.n, "nnz": A.nnz, "rp": rp, "ci": ci, "va": va, "h": h, "b": b,
+                    "x": torch.zeros_like(b), "xs": xs})
+    torch.cuda.synchronize()
+    return out
+
+
+def _solve_sequential(systems, stream):
+    """Plain FP64 CG, one system after another (one cooperative launch each);
+    returns (device seconds, iterations per system)."""
+    import torch
+    import paper_2112_10823_gb300 as cg
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record(stream)
+    for s in systems:
+        s["x"].zero_()
+        r = cg.cg_solve(s["h"], s["b"], s["x"], tol=TOL, maxit=10 * s["n"])
+        assert r.status == cg.CG_OK, r
+        its.append(r.iters)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1000.0, its
+
+
+def run_batch(args):
+    """Many uneven systems per step in one persistent launch (batched API)."""
+    import torch
+    import paper_2112_10823_gb300 as cg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    systems = _batch_systems(args.seed, args.batch_count, dev)
+    count = len(systems)
+    mixed = args.precision == "mixed"
+    hbm_peak, peak_kind = peaks()
+    energy = Energy(0)
+
+    # plain FP64 CG on the same GPU, system after system
+    _solve_sequential(systems, stream)
+    x64 = [s["x"].clone() for s in systems]
+    j0 = energy.read_j()
+    t_seq, its64 = 0.0, None
+    for _ in range(args.steps):
+        dt, its64 = _solve_sequential(systems, stream)
+        t_seq += dt
+    j1 = energy.read_j()
+    seq = {"solves_per_s": count * args.steps / t_seq, "ms_per_batch": 1000.0 * t_seq / args.steps,
+           "joules_per_solve": (j1 - j0) / (count * args.steps) if j0 is not None and j1 is not None else None,
+           "launches_per_batch": count}
+
+    bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=0, validate=False,
+                  budget_bytes=int(args.budget_gb * 2**30), max_systems=max(1024, count))
+
+    def step():
+        reqs = [cg.Request(s["rp"], s["ci"], s["va"], s["b"], s["x"], tol=TOL, maxit=10 * s["n"], tag=i)
+                for i, s in enumerate(systems)]
+        res = bt.wait_all(bt.submit(reqs))
+        bad = [r for r in res if r.status != cg.CG_OK or r.relres > TOL]
+        assert not bad, bad[:3]
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    st0 = bt.stats()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    with ClockSampler(0) as clk:
+        j0 = energy.read_j()
+        tw0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k)
+            torch.cuda.synchronize()
+            res = step()
+        t_wall = time.perf_counter() - tw0
+        j1 = energy.read_j()
+    st1 = bt.stats()
+    rounds = st1["rounds"] - st0["rounds"]
+    dev_s = (st1["round_ms_total"] - st0["round_ms_total"]) / 1000.0
+    value = count * args.steps / dev_s
+    iters = [r.iters for r in res]
+    groups = [r.group for r in res]
+    err = max(float(torch.linalg.vector_norm(s["x"] - x) / torch.linalg.vector_norm(x)) for s, x in zip(systems, x64))
+    bytes_batch = sum(solve_bytes(s["n"], s["nnz"], it, mixed) for s, it in zip(systems, iters))
+    flops_batch = sum(solve_flops(s["n"], s["nnz"], it, mixed) for s, it in zip(systems, iters))
+    per_round = dev_s / rounds
+    achieved = bytes_batch * args.steps / dev_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {count} Q1 27-point FE systems, grid edges uniform in [8, 48], "
+                               f"lognormal rho (sigma=1), own b per system, "
+                               f"{'mixed precision' if mixed else 'FP64'}, one persistent launch per batch "
+                               f"(CUDA graph), CG to 1e-10",
+                   "systems": count, "sum_n": int(sum(s["n"] for s in systems)),
+                   "sum_nnz": int(sum(s["nnz"] for s in systems)), "iters_min": min(iters), "iters_max": max(iters),
+                   "groups": {str(g): groups.count(g) for g in sorted(set(groups))},
+                   "rounds_per_step": rounds / args.steps, "graph": bool(st1["graph"]),
+                   "l2": "flushed before every step (256 MiB write); the batch's matrices exceed L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}>",
+                     "gflops": flops_batch * args.steps / dev_s / 1e9, "round_ms": 1000.0 * per_round},
+        "accuracy": {"max_relres_true": max(r.relres for r in res),
+                     "max_rel_diff_vs_fp64_cg_solve": err},
+        "fp64_sequential": seq,
+        "speedup_vs_fp64_sequential": value / seq["solves_per_s"],
+        "energy": {"joules_per_solve": (j1 - j0) / (count * args.steps) if j0 is not None and j1 is not None else None,
+                   "source": "NVML board energy (whole steps, host admission included)"},
+        "e2e": {"value": count * args.steps / t_wall, "unit": "solves/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(sum(8 * 0 for _ in systems)),
+                "note": "wall clock through cg_batch_submit/wait with device-resident inputs: "
+                        "admission (host partition, device copies) included"},
+        "gpu_launches": int(rounds + (count * args.steps if mixed else 0)),
+        "clocks": clk.summary(),
+        "gpu": {"name": torch.cuda.get_device_name(dev), "uuid": gpu_uuid(0)},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    bt.close()
+
+
+def run_serve(args):
+    """Continuous batching of a Poisson request stream (served API), against
+    a FIFO server of plain FP64 CG solves on the same GPU."""
+    import torch
+    import fe_inputs as fi
+    import paper_2112_10823_gb300 as cg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    mixed = args.precision == "mixed"
+    count = max(1, int(round(args.serve_rate * args.serve_seconds)))
+    t_arr, edges = fi.arrivals(args.seed, count, args.serve_rate)
+    # request i solves the pool system of its edge with right-hand side k = i % 4
+    pool = {}
+    for N in sorted(set(int(e) for e in edges)):
+        sd = fi.system_seed(args.seed, 100000 + N)
+        A = fi.q1(N, SIGMA, sd)
+        rp, ci, va = _upload(A, dev)
+        h = cg.cg_create(rp, ci, va)
+        bs = []
+        for k in range(4):
+            xs = torch.from_numpy(fi.xstar(fi.system_seed(sd, k), A.n)).to(dev)
+            b = torch.empty_like(xs)
+            cg.cg_spmv(h, xs, b)
+            bs.append(b)
+        pool[N] = {"n": A.n, "nnz": A.nnz, "rp": rp, "ci": ci, "va": va, "h": h, "b": bs}
+    torch.cuda.synchronize()
+    energy = Energy(0)
+
+    # FIFO server of plain FP64 CG: measured service time of every (edge, rhs)
+    # pair, then the single-server queue over the same arrival times
+    service = {}
+    x = None
+    for N, P in pool.items():
+        x = torch.zeros(P["n"], dtype=torch.float64, device=dev)
+        for k in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            r = cg.cg_solve(P["h"], P["b"][k], x, tol=TOL, maxit=10 * P["n"])
+            e1.record(stream)
+            e1.synchronize()
+            assert r.status == cg.CG_OK
+            service[(N, k)] = e0.elapsed_time(e1) / 1000.0
+    fin, lat64, busy = 0.0, [], 0.0
+    for i in range(count):
+        sv = service[(int(edges[i]), i % 4)]
+        fin = max(fin, t_arr[i]) + sv
+        busy += sv
+        lat64.append(fin - t_arr[i])
+    fifo = {"solves_per_s": count / fin, "p50_ms": 1000 * float(np.percentile(lat64, 50)),
+            "p99_ms": 1000 * float(np.percentile(lat64, 99)), "capacity_solves_per_s": count / busy,
+            "note": "single FIFO server of cg_solve (FP64, whole GPU per solve): measured service time per "
+                    "(edge, rhs) pair applied to the same arrival times"}
+
+    bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=args.chunk,
+                  validate=False, budget_bytes=int(args.budget_gb * 2**30), max_systems=1024)
+    outs = [torch.zeros(pool[int(N)]["n"], dtype=torch.float64, device=dev) for N in edges]
+    reqs = [cg.Request(pool[int(N)]["rp"], pool[int(N)]["ci"], pool[int(N)]["va"], pool[int(N)]["b"][i % 4],
+                       outs[i], tol=TOL, maxit=10 * pool[int(N)]["n"], tag=i) for i, N in enumerate(edges)]
+    # warm-up: one request of each edge
+    warm = {}
+    for i, N in enumerate(edges):
+        warm.setdefault(int(N), i)
+    bt.wait_all(bt.submit([reqs[i] for i in warm.values()]))
+    st0 = bt.stats()
+    depth = []
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            s = bt.stats()
+            depth.append((s["pending"], s["resident"]))
+            time.sleep(0.01)
+
+    th = threading.Thread(target=sample, daemon=True)
+    tickets = []
+    with ClockSampler(0) as clk:
+        j0 = energy.read_j()
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(count):
+            d = t0 + t_arr[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(bt.submit([reqs[i]])[0])
+        res = bt.wait_all(tickets)
+        t_end = time.perf_counter() - t0
+        stop.set()
+        th.join()
+        j1 = energy.read_j()
+    st1 = bt.stats()
+    bad = [r for r in res if r.status != cg.CG_OK or r.relres > TOL]
+    assert not bad, bad[:3]
+    lat = [r.latency_ms for r in res]
+    first = min(r.submit_ms for r in res)
+    last = max(r.done_ms for r in res)
+    value = count / ((last - first) / 1000.0)
+    dev_s = (st1["round_ms_total"] - st0["round_ms_total"]) / 1000.0
+    bytes_all = sum(solve_bytes(pool[int(edges[r.tag])]["n"], pool[int(edges[r.tag])]["nnz"], r.iters, mixed)
+                    for r in res)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_all / dev_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": count, "warmup": len(warm),
+        "ms_per_step": (last - first) / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"served stream: Poisson arrivals at {args.serve_rate:g} req/s for "
+                               f"{args.serve_seconds:g} s, Q1 27-point FE systems with grid edge lognormal in "
+                               f"[16, 96], {'mixed precision' if mixed else 'FP64'}, CG to 1e-10, "
+                               f"{args.budget_gb:g} GB device budget, {args.chunk} steps per system per round",
+                   "requests": count, "distinct_edges": len(pool), "rhs_per_edge": 4,
+                   "mean_nnz": float(np.mean([pool[int(N)]["nnz"] for N in edges]))},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(np.max(lat))},
+        "offered_solves_per_s": args.serve_rate,
+        "queue": {"max_pending": max(d[0] for d in depth) if depth else None,
+                  "max_resident": max(d[1] for d in depth) if depth else None,
+                  "bytes_peak": st1["bytes_peak"], "rounds": st1["rounds"] - st0["rounds"]},
+        "fp64_fifo": fifo,
+        "speedup_vs_fp64_fifo": value / fifo["solves_per_s"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}>",
+                     "device_busy_frac": dev_s / t_end},
+        "energy": {"joules_per_solve": (j1 - j0) / count if j0 is not None and j1 is not None else None,
+                   "fp64_fifo_joules_per_solve": None, "source": "NVML board energy over the whole stream"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "request submission to solution written, through cg_batch_submit/wait"},
+        "gpu_launches": int(st1["rounds"] - st0["rounds"] + (count if mixed else 0)),
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    bt.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

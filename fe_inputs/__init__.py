@@ -166,6 +166,32 @@ def xstar(seed: int, n: int) -> np.ndarray:
     return uniform(seed, STREAM_XSTAR, n, -1.0, 1.0)
 
 
+def system_seed(seed: int, i: int) -> int:
+    """Seed of system i of a batch or request stream drawn from `seed`
+    (each system has its own densities and manufactured solution)."""
+    return draw_u64(seed, STREAM_BATCH, 2 * i + 1) & 0x7FFFFFFFFFFFFFFF
+
+
+def batch_edges(seed: int, count: int, lo: int = 8, hi: int = 48) -> np.ndarray:
+    """Grid edges of a batch: N_i uniform on {lo, ..., hi}."""
+    u = np.array([draw_u64(seed, STREAM_BATCH, 2 * i) for i in range(count)], dtype=np.uint64)
+    return (lo + (u % np.uint64(hi - lo + 1)).astype(np.int64)).astype(np.int64)
+
+
+def arrivals(seed: int, count: int, rate: float, lo: int = 16, hi: int = 96,
+             mu: float | None = None, sigma: float = 0.448) -> tuple[np.ndarray, np.ndarray]:
+    """A request stream: Poisson arrivals at `rate` per second (times in s of
+    seeded exponential gaps) and grid edges lognormal, ln N ~ N(mu, sigma^2)
+    with mu = ln sqrt(lo hi) by default, rounded and clipped to [lo, hi]."""
+    if mu is None:
+        mu = 0.5 * (np.log(lo) + np.log(hi))
+    u = uniform(seed, STREAM_ARRIVALS, count, 0.0, 1.0)
+    gaps = -np.log1p(-u) / rate
+    z = normal(seed, STREAM_ARRIVALS + 100, count)
+    edges = np.clip(np.rint(np.exp(mu + sigma * z)), lo, hi).astype(np.int64)
+    return np.cumsum(gaps), edges
+
+
 def random_csr(n: int, seed: int, min_len: int = 0, max_len: int = 40,
                empty_frac: float = 0.1, long_rows: tuple[int, ...] = (),
                integer: bool = False, ncols: int | None = None) -> CSR:

@@ -181,6 +181,137 @@ int cg_dot_noalloc(int64_t n, const double* x, const double* y, double* result, 
  */
 int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status);
 
+/* ------------------------------------------------------------------------
+ * Batched and served solves: many independent systems on one GPU.
+ *
+ * The paper solves one system at a time (Sec. 5.3); these entry points
+ * extend the same classical CG to many independent SPD systems sharing one
+ * GPU.  A batch object owns a device memory budget, a table of resident
+ * systems and a worker thread.  cg_batch_submit() queues requests and
+ * returns at once; the worker admits queued requests in arrival order as
+ * memory and slots free up (copying each matrix and right-hand side into the
+ * budget), and advances every resident system with one persistent
+ * cooperative kernel launch per round (replayed from a captured CUDA graph):
+ * each CTA takes systems from a queue; a large system is solved by a group
+ * of CTAs with its own group barrier, most by one CTA.  With chunk_iters > 0
+ * each round advances every system at most chunk_iters steps, so requests
+ * that arrive meanwhile join at the next round (continuous batching); with
+ * chunk_iters = 0 a round runs every resident system to its end (one launch
+ * for a batch that fits the budget).  A finished system's solution is
+ * copied to the request's x and its memory released before the next round.
+ *
+ * The arithmetic of every system is that of cg_solve with the batch's
+ * precision (x0 = 0; the same stopping test and outputs).  How many CTAs
+ * solve a system (its "group") is chosen from the system alone (its rows,
+ * entries and row lengths), never from the rest of the batch, so a system
+ * gives the same bits alone and in any mix on the same batch object.
+ * ---------------------------------------------------------------------- */
+
+typedef struct cg_batch_ctx* cg_batch;
+
+typedef struct {
+  int32_t device;          /* CUDA device ordinal; -1 = the current device */
+  int32_t precision;       /* cg_precision of every system of the batch */
+  int64_t budget_bytes;    /* device memory for resident systems (matrices, vectors,
+                              partition tables); 0 = half of the free memory at creation */
+  int32_t max_systems;     /* resident systems at most (default 1024) */
+  int32_t chunk_iters;     /* steps per system per round; 0 = until the system ends */
+  int32_t replace_every;   /* CG_PREC_MIXED residual-replacement period (default 50) */
+  int32_t wait_limit_ms;   /* bound on any device-side wait (default 2000) */
+  int32_t max_pending;     /* queued requests not yet admitted (default 65536) */
+  int32_t use_graph;       /* 1 (default): replay each round from a captured CUDA graph */
+  int32_t group_override;  /* > 0: every system uses this many CTAs (tests); 0 = automatic */
+  int32_t validate;        /* 1 (default): check each request's CSR on the host */
+  int32_t reserved[6];     /* zero */
+} cg_batch_opts;
+
+/* One system to solve: A x = b from x0 = 0. */
+typedef struct {
+  cg_csr csr;              /* the matrix (host or device arrays) */
+  int64_t n, nnz;
+  const double* b;         /* n doubles, host or device */
+  double* x;               /* n doubles, host or device: receives the solution */
+  double tol;              /* relative residual target (as cg_solve) */
+  int64_t maxit;           /* step limit (as cg_solve) */
+  uint64_t tag;            /* caller's value, returned in the result */
+} cg_request;
+
+typedef struct {
+  uint64_t ticket;
+  uint64_t tag;
+  int32_t done;            /* 1 once the request has ended (status and x final) */
+  int32_t status;          /* as cg_solve: CG_OK, CG_ENOTCONV, CG_EBREAKDOWN, CG_ETIMEOUT,
+                              or CG_EINVAL / CG_ENOMEM / CG_ECUDA if it could not be admitted */
+  int64_t iters;           /* steps taken */
+  double relres;           /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+  double submit_ms;        /* host times in ms since the batch object was created: */
+  double admit_ms;         /*   queued, resident on the device, */
+  double done_ms;          /*   solution written to x */
+  int32_t group;           /* CTAs that solved the system */
+  int32_t rounds;          /* rounds (kernel launches) the system took part in */
+} cg_result;
+
+typedef struct {
+  int64_t rounds;          /* persistent kernel launches so far */
+  int64_t submitted, admitted, completed;
+  int64_t pending;         /* queued, not yet admitted */
+  int64_t resident;        /* on the device now */
+  int64_t bytes_in_use, bytes_peak, budget_bytes;
+  int32_t graph;           /* 1 if rounds are replayed from a CUDA graph */
+  int32_t nblocks;         /* CTAs of the persistent kernel */
+  double round_ms_total;   /* device time of all rounds (CUDA events around each) */
+  double last_round_ms;    /* device time of the last round */
+} cg_batch_stats;
+
+/* Fill *o with the defaults above. */
+void cg_batch_opts_default(cg_batch_opts* o);
+
+/* Create a batch object: reserves budget_bytes of device memory, the system
+ * table and the worker thread.  opts may be NULL.  On failure *out is NULL
+ * and cg_batch_last_error(NULL) gives the reason. */
+int cg_batch_create(cg_batch* out, const cg_batch_opts* opts);
+
+/* Stop the worker (after the round in flight), drop queued requests and
+ * release everything.  Pointers of unfinished requests are never touched
+ * again.  NULL is accepted. */
+int cg_batch_destroy(cg_batch b);
+
+/*
+ * Queue `count` requests; tickets[i] receives the ticket of reqs[i].
+ * Non-blocking: the matrices are copied when the worker admits a request,
+ * so every array a request names (csr arrays, b, x) must stay valid and
+ * unchanged until its result is done.  Device arrays must already hold
+ * their values (synchronise the stream that wrote them before submitting):
+ * the worker copies them on a stream of its own.  Returns CG_EINVAL (bad request: NULL
+ * pointer, n or nnz out of range, tol < 0, maxit < 0; nothing is queued),
+ * CG_ENOMEM (a request needs more memory than the whole budget; nothing is
+ * queued) or CG_EBUSY (the pending queue is full; nothing is queued).
+ * A CSR that fails validation is reported in that request's result
+ * (status CG_EINVAL) when the worker reaches it.
+ */
+int cg_batch_submit(cg_batch b, const cg_request* reqs, int32_t count, uint64_t* tickets);
+
+/* Result of a ticket so far: res->done = 0 while it is queued or running.
+ * Once a done result has been returned, the ticket is forgotten (a later
+ * poll gives CG_EINVAL). */
+int cg_batch_poll(cg_batch b, uint64_t ticket, cg_result* res);
+
+/* As cg_batch_poll, but waits up to timeout_ms (< 0: without limit) for the
+ * request to end; res->done tells whether it did. */
+int cg_batch_wait(cg_batch b, uint64_t ticket, int32_t timeout_ms, cg_result* res);
+
+/* Counters of the batch object (a consistent snapshot). */
+int cg_batch_get_stats(cg_batch b, cg_batch_stats* st);
+
+/* Group size (CTAs) the batch object would give an n-row system with the
+ * row pointers row_ptr (host, n+1 entries, base 0 or 1): the automatic
+ * choice from the system alone. */
+int cg_batch_group_for(cg_batch b, const int32_t* row_ptr, int64_t n, int32_t* group);
+
+/* Message of the last failure on b (or of the last failed cg_batch_create on
+ * this thread when b is NULL). */
+const char* cg_batch_last_error(cg_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,36 @@ class cg_opts(ctypes.Structure):
                 ("wait_limit_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class cg_batch_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("max_systems", ctypes.c_int32), ("chunk_iters", ctypes.c_int32),
+                ("replace_every", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("group_override", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class cg_request(ctypes.Structure):
+    _fields_ = [("csr", cg_csr), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("tol", ctypes.c_double), ("maxit", ctypes.c_int64),
+                ("tag", ctypes.c_uint64)]
+
+
+class cg_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("done", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("iters", ctypes.c_int64), ("relres", ctypes.c_double),
+                ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("group", ctypes.c_int32), ("rounds", ctypes.c_int32)]
+
+
+class cg_batch_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("resident", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("graph", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("round_ms_total", ctypes.c_double),
+                ("last_round_ms", ctypes.c_double)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libcg.so is not built ({LIB_PATH}); run paper_2112_10823_gb300.build.build() "
@@ -68,6 +98,24 @@ def _load() -> ctypes.CDLL:
     lib.cg_dot_noalloc.argtypes = [i64, vp, vp, vp, vp]
     lib.cg_selftest_wait_timeout.restype = ctypes.c_int
     lib.cg_selftest_wait_timeout.argtypes = [i32, P(i32)]
+    lib.cg_batch_opts_default.restype = None
+    lib.cg_batch_opts_default.argtypes = [P(cg_batch_opts)]
+    lib.cg_batch_create.restype = ctypes.c_int
+    lib.cg_batch_create.argtypes = [P(vp), P(cg_batch_opts)]
+    lib.cg_batch_destroy.restype = ctypes.c_int
+    lib.cg_batch_destroy.argtypes = [vp]
+    lib.cg_batch_submit.restype = ctypes.c_int
+    lib.cg_batch_submit.argtypes = [vp, P(cg_request), i32, P(ctypes.c_uint64)]
+    lib.cg_batch_poll.restype = ctypes.c_int
+    lib.cg_batch_poll.argtypes = [vp, ctypes.c_uint64, P(cg_result)]
+    lib.cg_batch_wait.restype = ctypes.c_int
+    lib.cg_batch_wait.argtypes = [vp, ctypes.c_uint64, i32, P(cg_result)]
+    lib.cg_batch_get_stats.restype = ctypes.c_int
+    lib.cg_batch_get_stats.argtypes = [vp, P(cg_batch_stats)]
+    lib.cg_batch_group_for.restype = ctypes.c_int
+    lib.cg_batch_group_for.argtypes = [vp, vp, i64, P(i32)]
+    lib.cg_batch_last_error.restype = ctypes.c_char_p
+    lib.cg_batch_last_error.argtypes = [vp]
     return lib
 
 
@@ -278,3 +326,151 @@ def cg_selftest_wait_timeout(limit_ms: int = 200) -> int:
 
 def last_error(h: Handle | None = None) -> str:
     return lib.cg_last_error(h._h if h is not None else None).decode(errors="replace")
+
+
+# ----------------------------------------------------------- batched solves
+
+@dataclass
+class Request:
+    """One system A x = b (x0 = 0) for a Batch.  Arrays are host (numpy / CPU
+    torch) or CUDA tensors; the Batch keeps references to them until the
+    request's result is done (the library reads b and the matrix at admission
+    and writes x at the end)."""
+    row_ptr: object
+    col_idx: object
+    val: object
+    b: object
+    x: object
+    tol: float = 1e-10
+    maxit: int | None = None
+    index_base: int = 0
+    tag: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0]) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.shape[0])
+
+
+@dataclass
+class BatchResult:
+    ticket: int
+    tag: int
+    done: bool
+    status: int
+    iters: int
+    relres: float
+    submit_ms: float
+    admit_ms: float
+    done_ms: float
+    group: int
+    rounds: int
+
+    @property
+    def latency_ms(self) -> float:
+        return self.done_ms - self.submit_ms
+
+
+def _result(r: cg_result) -> BatchResult:
+    return BatchResult(int(r.ticket), int(r.tag), bool(r.done), int(r.status), int(r.iters), float(r.relres),
+                       float(r.submit_ms), float(r.admit_ms), float(r.done_ms), int(r.group), int(r.rounds))
+
+
+class Batch:
+    """Many independent systems on one GPU (wraps ``cg_batch``): requests are
+    queued by submit(), admitted by the library's worker as the memory budget
+    allows, and advanced together by one persistent kernel launch per round."""
+
+    def __init__(self, precision: int = CG_PREC_FP64, budget_bytes: int = 0, max_systems: int = 1024,
+                 chunk_iters: int = 0, replace_every: int = 50, wait_limit_ms: int = 2000,
+                 max_pending: int = 65536, use_graph: bool = True, group_override: int = 0,
+                 validate: bool = True, device: int = -1):
+        o = cg_batch_opts()
+        lib.cg_batch_opts_default(ctypes.byref(o))
+        o.device, o.precision, o.budget_bytes = int(device), int(precision), int(budget_bytes)
+        o.max_systems, o.chunk_iters, o.replace_every = int(max_systems), int(chunk_iters), int(replace_every)
+        o.wait_limit_ms, o.max_pending, o.use_graph = int(wait_limit_ms), int(max_pending), 1 if use_graph else 0
+        o.group_override, o.validate = int(group_override), 1 if validate else 0
+        out = ctypes.c_void_p(0)
+        st = lib.cg_batch_create(ctypes.byref(out), ctypes.byref(o))
+        if st != CG_OK:
+            raise CGError(st, lib.cg_batch_last_error(None).decode(errors="replace"))
+        self._b = out
+        self._keep: dict[int, Request] = {}
+
+    def _check(self, st: int) -> None:
+        if st != CG_OK:
+            raise CGError(st, lib.cg_batch_last_error(self._b).decode(errors="replace"))
+
+    def submit(self, reqs: list[Request]) -> list[int]:
+        """Queue the requests; returns their tickets.  CUDA arrays must hold
+        their values when the library copies them, so torch's current stream
+        is synchronised first if any request names a CUDA array."""
+        if any(_is_cuda(a) for r in reqs for a in (r.row_ptr, r.col_idx, r.val, r.b, r.x)):
+            import torch
+            torch.cuda.current_stream().synchronize()
+        arr = (cg_request * len(reqs))()
+        for i, r in enumerate(reqs):
+            on_dev = _is_cuda(r.row_ptr)
+            if on_dev != _is_cuda(r.col_idx) or on_dev != _is_cuda(r.val):
+                raise ValueError("row_ptr, col_idx and val must all be host or all be CUDA")
+            arr[i].csr = cg_csr(_ptr(r.row_ptr), _ptr(r.col_idx), _ptr(r.val), int(r.index_base), 1 if on_dev else 0)
+            arr[i].n, arr[i].nnz = r.n, r.nnz
+            arr[i].b, arr[i].x = _ptr(r.b), _ptr(r.x)
+            arr[i].tol = float(r.tol)
+            arr[i].maxit = 10 * r.n if r.maxit is None else int(r.maxit)
+            arr[i].tag = int(r.tag)
+        tickets = (ctypes.c_uint64 * max(1, len(reqs)))()
+        self._check(lib.cg_batch_submit(self._b, arr, len(reqs), tickets))
+        out = [int(tickets[i]) for i in range(len(reqs))]
+        for t, r in zip(out, reqs):
+            self._keep[t] = r
+        return out
+
+    def poll(self, ticket: int) -> BatchResult:
+        return self.wait(ticket, 0)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> BatchResult:
+        r = cg_result()
+        self._check(lib.cg_batch_wait(self._b, int(ticket), int(timeout_ms), ctypes.byref(r)))
+        res = _result(r)
+        if res.done:
+            self._keep.pop(ticket, None)
+        return res
+
+    def wait_all(self, tickets: list[int], timeout_ms: int = -1) -> list[BatchResult]:
+        return [self.wait(t, timeout_ms) for t in tickets]
+
+    def stats(self) -> dict:
+        s = cg_batch_stats()
+        self._check(lib.cg_batch_get_stats(self._b, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in cg_batch_stats._fields_}
+
+    def group_for(self, row_ptr) -> int:
+        import numpy as np
+        rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int32))
+        g = ctypes.c_int32(0)
+        self._check(lib.cg_batch_group_for(self._b, _ptr(rp), int(rp.shape[0]) - 1, ctypes.byref(g)))
+        return g.value
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) is not None and self._b.value:
+            lib.cg_batch_destroy(self._b)
+            self._b = ctypes.c_void_p(0)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False

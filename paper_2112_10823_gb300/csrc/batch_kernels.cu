@@ -1,0 +1,86 @@
+// The batched persistent solve: many systems in one cooperative launch.
+// Each CTA takes tasks (a system and its rank in the system's group of CTAs)
+// from a queue; the CG arithmetic of every task is the single-system solve's
+// (cg_solve.cuh).
+#include <mutex>
+#include <set>
+#include <utility>
+#include "cg_solve.cuh"
+
+namespace cgk {
+
+// Many systems in one persistent launch: each CTA takes tasks (a system and
+// its rank in the system's group) from the queue until it is empty.  Group
+// tasks come first in the queue and all fit in the grid, so the ranks of a
+// group start together; the rest are one-CTA tasks, taken in queue order as
+// CTAs free up.  Between tasks the whole CTA (producer included) joins, the
+// producer having drained its copies, and the ring barriers are reset.
+template <bool kMixed>
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __grid_constant__ BatchParams B) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const RingSmem sm{smem_raw};
+  __shared__ int32_t task_id;
+  bool reinit = false;
+  for (;;) {
+    if (threadIdx.x == 0) task_id = atomicAdd(B.next, 1);
+    __syncthreads();
+    const int t = task_id;
+    if (t >= B.queue->ntasks) break;
+    const BatchTask tk = B.queue->task[t];
+    const SolveParams& P = B.sys[tk.sys];
+    CtaStream cs;
+    stream_setup(sm, cs, P.A, tk.rank, reinit);
+    reinit = true;
+    if (threadIdx.x >= kConsumers) solve_producer<kMixed>(sm, cs, P);
+    else solve_consumers<kMixed>(sm, cs, P, tk.rank);
+    __syncthreads();  // producer drained, consumers done: the CTA is free
+  }
+}
+
+namespace {
+cudaError_t batch_smem_attr(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kernel, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess) done.insert({kernel, dev});
+  return e;
+}
+}  // namespace
+
+int batch_blocks_per_sm(bool mixed) {
+  int nb = 0;
+  const void* k = mixed ? reinterpret_cast<const void*>(cg_batch_kernel<true>)
+                        : reinterpret_cast<const void*>(cg_batch_kernel<false>);
+  cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, RingSmem::kBytes);
+  return e == cudaSuccess ? nb : -1;
+}
+
+// Cooperative launch (all CTAs co-resident: the ranks of a group wait on
+// each other), through cudaLaunchKernelEx so that it can be captured in a
+// CUDA graph.
+cudaError_t launch_batch(const BatchParams& B, bool mixed, int nblocks, cudaStream_t s) {
+  const void* k = mixed ? reinterpret_cast<const void*>(cg_batch_kernel<true>)
+                        : reinterpret_cast<const void*>(cg_batch_kernel<false>);
+  cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = RingSmem::kBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<BatchParams*>(&B)};
+  return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+}  // namespace cgk

@@ -10,12 +10,91 @@
 
 #include "../../include/cg.h"
 #include "cg_internal.h"
+#include "host_util.h"
+
+using cgh::Partition;
+using cgh::build_partition;
 
 namespace cgk {
 cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s);
 cudaError_t launch_dot_noalloc(int64_t n, const double* x, const double* y, double* out, cudaStream_t s);
 int64_t dot_noalloc_max_n();
 }
+
+namespace cgh {
+
+// Row partition of the persistent kernels.  Rows are split into `nblocks`
+// contiguous CTA ranges of about equal cost (stored entries + kRowCost per
+// row, the per-row vector work), and each CTA range into steps (see
+// cg_internal.h): up to 32 rows of <= 32 entries (one lane per row), up to 16
+// rows of <= 64 entries (two lanes per row), never more than kStepNnz entries,
+// or one longer row.  Two sentinel steps follow the last one (the kernels
+// read descriptors ahead).
+constexpr int64_t kRowCost = 6;
+
+int64_t cost_split(const std::vector<int32_t>& rp, int64_t lo_row, int64_t hi_row, int64_t part, int64_t parts) {
+  // first row i in [lo_row, hi_row] with cost(lo_row, i) >= cost(lo_row, hi_row) * part / parts
+  const int64_t c0 = static_cast<int64_t>(rp[lo_row]) + kRowCost * lo_row;
+  const int64_t c1 = static_cast<int64_t>(rp[hi_row]) + kRowCost * hi_row;
+  const int64_t goal = c0 + ((c1 - c0) * part) / parts;
+  int64_t lo = lo_row, hi = hi_row;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (static_cast<int64_t>(rp[mid]) + kRowCost * mid >= goal) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partition& P) {
+  const int64_t kPairMax = 2 * cgk::kLaneMax;
+  while (row < end) {
+    const int64_t len0 = rp[row + 1] - rp[row];
+    if (len0 > kPairMax) {  // a long row: one step, walked piece by piece
+      P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), rp[row], rp[row + 1]));
+      P.step_mode.push_back(cgk::kLongRow);
+      ++row;
+      continue;
+    }
+    const int64_t start = row;
+    int64_t cnt = 0, maxlen = 0;
+    while (row < end) {
+      const int64_t len = rp[row + 1] - rp[row];
+      if (len > kPairMax || cnt + len > cgk::kStepNnz) break;
+      const int64_t nm = std::max(maxlen, len);
+      const int64_t cap = nm <= cgk::kLaneMax ? 32 : 16;
+      if (row - start + 1 > cap) break;
+      cnt += len;
+      maxlen = nm;
+      ++row;
+    }
+    P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
+    const bool lane_mode = maxlen <= cgk::kLaneMax;
+    const int64_t wmax = lane_mode ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
+    P.step_mode.push_back((lane_mode ? cgk::kLanePerRow : cgk::kPairPerRow) |
+                          static_cast<int32_t>(wmax << cgk::kWmaxShift));
+  }
+}
+
+void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P) {
+  P.step.clear();
+  P.step_mode.clear();
+  P.block_step.assign(static_cast<size_t>(nblocks) + 1, 0);
+  P.block_row.assign(static_cast<size_t>(nblocks) + 1, 0);
+  for (int b = 0; b <= nblocks; ++b) P.block_row[b] = static_cast<int32_t>(cost_split(rp, 0, n, b, nblocks));
+  P.block_row[nblocks] = static_cast<int32_t>(n);
+  for (int b = 0; b < nblocks; ++b) {
+    P.block_step[b] = static_cast<int32_t>(P.step.size());
+    warp_steps(rp, P.block_row[b], P.block_row[b + 1], P);
+  }
+  P.block_step[nblocks] = static_cast<int32_t>(P.step.size());
+  for (int t = 0; t < 2; ++t) {  // sentinels
+    P.step.push_back(make_int4(static_cast<int>(n), static_cast<int>(n), rp[n], rp[n]));
+    P.step_mode.push_back(cgk::kLanePerRow);
+  }
+}
+
+}  // namespace cgh
 
 struct cg_ctx {
   int device = 0;
@@ -97,84 +176,6 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Row partition of the persistent kernels.  Rows are split into `nblocks`
-// contiguous CTA ranges of about equal cost (stored entries + kRowCost per
-// row, the per-row vector work), and each CTA range into steps (see
-// cg_internal.h): up to 32 rows of <= 32 entries (one lane per row), up to 16
-// rows of <= 64 entries (two lanes per row), never more than kStepNnz entries,
-// or one longer row.  Two sentinel steps follow the last one (the kernels
-// read descriptors ahead).
-constexpr int64_t kRowCost = 6;
-
-struct Partition {
-  std::vector<int4> step;
-  std::vector<int32_t> step_mode;
-  std::vector<int32_t> block_step;
-  std::vector<int32_t> block_row;
-};
-
-int64_t cost_split(const std::vector<int32_t>& rp, int64_t lo_row, int64_t hi_row, int64_t part, int64_t parts) {
-  // first row i in [lo_row, hi_row] with cost(lo_row, i) >= cost(lo_row, hi_row) * part / parts
-  const int64_t c0 = static_cast<int64_t>(rp[lo_row]) + kRowCost * lo_row;
-  const int64_t c1 = static_cast<int64_t>(rp[hi_row]) + kRowCost * hi_row;
-  const int64_t goal = c0 + ((c1 - c0) * part) / parts;
-  int64_t lo = lo_row, hi = hi_row;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) / 2;
-    if (static_cast<int64_t>(rp[mid]) + kRowCost * mid >= goal) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
-void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partition& P) {
-  const int64_t kPairMax = 2 * cgk::kLaneMax;
-  while (row < end) {
-    const int64_t len0 = rp[row + 1] - rp[row];
-    if (len0 > kPairMax) {  // a long row: one step, walked piece by piece
-      P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), rp[row], rp[row + 1]));
-      P.step_mode.push_back(cgk::kLongRow);
-      ++row;
-      continue;
-    }
-    const int64_t start = row;
-    int64_t cnt = 0, maxlen = 0;
-    while (row < end) {
-      const int64_t len = rp[row + 1] - rp[row];
-      if (len > kPairMax || cnt + len > cgk::kStepNnz) break;
-      const int64_t nm = std::max(maxlen, len);
-      const int64_t cap = nm <= cgk::kLaneMax ? 32 : 16;
-      if (row - start + 1 > cap) break;
-      cnt += len;
-      maxlen = nm;
-      ++row;
-    }
-    P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
-    const bool lane_mode = maxlen <= cgk::kLaneMax;
-    const int64_t wmax = lane_mode ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
-    P.step_mode.push_back((lane_mode ? cgk::kLanePerRow : cgk::kPairPerRow) |
-                          static_cast<int32_t>(wmax << cgk::kWmaxShift));
-  }
-}
-
-void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P) {
-  P.step.clear();
-  P.step_mode.clear();
-  P.block_step.assign(static_cast<size_t>(nblocks) + 1, 0);
-  P.block_row.assign(static_cast<size_t>(nblocks) + 1, 0);
-  for (int b = 0; b <= nblocks; ++b) P.block_row[b] = static_cast<int32_t>(cost_split(rp, 0, n, b, nblocks));
-  P.block_row[nblocks] = static_cast<int32_t>(n);
-  for (int b = 0; b < nblocks; ++b) {
-    P.block_step[b] = static_cast<int32_t>(P.step.size());
-    warp_steps(rp, P.block_row[b], P.block_row[b + 1], P);
-  }
-  P.block_step[nblocks] = static_cast<int32_t>(P.step.size());
-  for (int t = 0; t < 2; ++t) {  // sentinels
-    P.step.push_back(make_int4(static_cast<int>(n), static_cast<int>(n), rp[n], rp[n]));
-    P.step_mode.push_back(cgk::kLanePerRow);
-  }
 }
 
 cgk::DevCsr dev_view(const cg_ctx* h) {
@@ -485,6 +486,9 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   P.maxit = maxit;
   P.replace_every = h->replace_every;
   P.wait_limit_ns = h->wait_limit_ns;
+  P.group = h->nblocks;
+  P.pad = 0;
+  P.chunk_iters = 0;
   e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: cooperative launch");
   e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(cgk::SolveCtrl), cudaMemcpyDeviceToHost, h->stream);

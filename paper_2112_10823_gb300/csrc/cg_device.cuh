@@ -218,24 +218,28 @@ __device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
   return fx_block_sum<1>(a, sc);
 }
 
-// ------------------------------------------------------------ grid barrier
+// ----------------------------------------------------------- group barrier
 
-// Bounded grid-wide barrier for a cooperative (co-resident) launch, split in
-// an arrive and a wait half so that a CTA can do independent work between
-// them.  Thread 0 of each CTA adds one arrival to a monotonic 64-bit counter
-// with release semantics and later spins with acquire loads until all CTAs of
-// this round have arrived; the fence afterwards makes every write that
-// preceded any CTA's arrival visible to all threads of this CTA.  A wait
-// longer than `limit_ns`, or an abort raised by another CTA, makes wait()
-// return false in every thread of the CTA (the caller then leaves the kernel).
+// Bounded barrier of the `count` CTAs that solve one system together (the
+// whole grid of a single-system solve, a group of CTAs in a batched solve;
+// all co-resident: the launch is cooperative).  Split in an arrive and a wait
+// half so that a CTA can do independent work between them.  Thread 0 of each
+// CTA adds one arrival to the system's monotonic 64-bit counter with release
+// semantics and later spins with acquire loads until all CTAs of this round
+// have arrived; the fence afterwards makes every write that preceded any
+// CTA's arrival visible to all threads of this CTA.  A wait longer than
+// `limit_ns`, or an abort raised by another CTA, makes wait() return false in
+// every thread of the CTA (the caller then abandons the solve).  A group of
+// one CTA needs only the CTA barrier.
 struct GridBarrier {
-  unsigned long long target = 0;
+  unsigned long long target = 0;  // counter value that completes the current round
+  unsigned int count = 1;         // CTAs in the group
 
   // All threads call; the CTA's writes before this point are published.
   __device__ __forceinline__ void arrive(SolveCtrl* ctrl) {
     cta_sync();
-    target += gridDim.x;
-    if (threadIdx.x == 0) {
+    target += count;
+    if (count > 1 && threadIdx.x == 0) {
       __threadfence();
       red_release_add_u64(&ctrl->barrier, 1ull);
     }
@@ -243,6 +247,7 @@ struct GridBarrier {
 
   __device__ __forceinline__ bool wait(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
                                        int32_t* flag_smem) {
+    if (count <= 1) return true;  // arrive() already synchronised the CTA
     if (threadIdx.x == 0) {
       int32_t ok = 1;
       unsigned long long t0 = 0;
@@ -313,19 +318,30 @@ struct CtaStream {
   int s0 = 0, s1 = 0;  // the CTA's steps [s0, s1)
 };
 
-// Initialise the barriers (all threads of the CTA call, then a full barrier).
-__device__ __forceinline__ void stream_setup(const RingSmem& sm, CtaStream& cs, const DevCsr& A) {
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Initialise the ring barriers for the CTA's share `rank` of A's partition
+// (all threads of the CTA call; ends with a full CTA barrier).  `reinit`:
+// the barriers hold a previous stream, already drained (a CTA taking another
+// task of a batched solve); they are invalidated first.
+__device__ __forceinline__ void stream_setup(const RingSmem& sm, CtaStream& cs, const DevCsr& A, int rank,
+                                             bool reinit = false) {
   if (threadIdx.x < kSlots) {
+    if (reinit) {
+      mbar_inval(sm.full(threadIdx.x));
+      mbar_inval(sm.empty(threadIdx.x));
+    }
     mbar_init(sm.full(threadIdx.x), 1);
     mbar_init(sm.empty(threadIdx.x), kConsumerWarps);
   }
-  if (threadIdx.x == 0) {
-    *sm.stop() = 0;
-    fence_mbar_init();
-  }
+  if (threadIdx.x == 0) *sm.stop() = 0;
+  if (threadIdx.x < kSlots) fence_mbar_init();
   __syncthreads();
-  cs.s0 = A.block_step[blockIdx.x];
-  cs.s1 = A.block_step[blockIdx.x + 1];
+  cs.s0 = A.block_step[rank];
+  cs.s1 = A.block_step[rank + 1];
+  cs.kb = cs.ke = cs.npieces = 0;
   if (cs.s1 > cs.s0) {
     cs.kb = A.step[cs.s0].z & ~3;
     cs.ke = A.step[cs.s1 - 1].w;

@@ -65,17 +65,24 @@ struct DevCsr {
   int64_t nnz;
 };
 
-// Control block of one solve, in device memory, cleared before each launch.
+// Control block of one solve, in device memory, cleared before its first
+// launch.  A solve may run over several launches (batched solves advance
+// each system a bounded number of steps per launch): the fields below
+// `phase` carry its state from one launch to the next.
+enum SolvePhase : int32_t { kPhaseNew = 0, kPhaseRunning = 1, kPhaseDone = 2 };
 struct SolveCtrl {
-  unsigned long long barrier;   // monotonic arrival counter of the grid barrier
+  unsigned long long barrier;   // monotonic arrival counter of the group barrier
   int32_t abort;                // set by any CTA that gives up (timeout)
   int32_t status;               // CG_* code
-  int64_t iters;
-  double rho;                   // r.r of the last iterate (recursive residual)
+  int64_t iters;                // steps done
+  double rho;                   // r.r of the current iterate (recursive residual)
   double bnorm2;                // b.b
   double relres_rec;            // sqrt(rho)/||b||
   double relres_true;           // ||b - A x|| / ||b||
   int32_t timeout_site;         // which wait gave up (diagnostics)
+  int32_t phase;                // SolvePhase
+  unsigned long long rounds;    // group-barrier rounds completed so far
+  int32_t slot;                 // partial-sum slot the next group sum uses
   int32_t pad;
 };
 
@@ -93,6 +100,26 @@ struct SolveParams {
   int64_t maxit;
   int64_t replace_every;        // mixed precision: true-residual period
   unsigned long long wait_limit_ns;  // bound on every device-side wait
+  int32_t group;                // CTAs that solve this system together (its partition's CTA count)
+  int32_t pad;
+  int64_t chunk_iters;          // steps per launch (<= 0: until the solve ends)
+};
+
+// Batched solves: one persistent launch over many systems.  Every CTA takes
+// tasks from a queue; a task is one CTA's share (rank) of one system.
+struct BatchTask {
+  int32_t sys;                  // index into the system table
+  int32_t rank;                 // 0 .. group-1
+};
+struct BatchQueue {
+  int32_t ntasks;
+  int32_t pad;
+  BatchTask task[1];            // ntasks entries (allocated to capacity)
+};
+struct BatchParams {
+  const SolveParams* sys;       // system table (one entry per slot)
+  const BatchQueue* queue;      // tasks of this launch, group tasks first
+  int32_t* next;                // next task to take (zeroed before each launch)
 };
 
 // Status codes (same values as include/cg.h).
@@ -109,6 +136,9 @@ cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStr
 cudaError_t launch_ewmul(int64_t n, const double* x, const double* y, double* z, cudaStream_t s);
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s);
 int solve_blocks_per_sm(bool mixed);   // occupancy of the persistent kernel
+// The batched solve (cooperative launch of `nblocks` CTAs, one per SM).
+cudaError_t launch_batch(const BatchParams& B, bool mixed, int nblocks, cudaStream_t s);
+int batch_blocks_per_sm(bool mixed);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
 // Shared-memory bytes of the streamed product (ring + scratch).

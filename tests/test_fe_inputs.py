@@ -100,3 +100,23 @@ def test_random_csr_edge_cases():
     assert A.row_ptr[0] == 0 and A.row_ptr[-1] == A.nnz
     B = fi.to_one_based(A)
     assert B.row_ptr[0] == 1 and B.index_base == 1
+
+
+def test_batch_edges_uniform_and_seeded():
+    e = fi.batch_edges(0, 4000)
+    assert e.min() >= 8 and e.max() <= 48
+    assert np.array_equal(e, fi.batch_edges(0, 4000))
+    assert not np.array_equal(e, fi.batch_edges(1, 4000))
+    counts = np.bincount(e - 8, minlength=41)
+    assert counts.min() > 0.6 * 4000 / 41 and counts.max() < 1.4 * 4000 / 41
+    assert fi.system_seed(0, 0) != fi.system_seed(0, 1)
+
+
+def test_arrivals_poisson_and_lognormal_edges():
+    t, e = fi.arrivals(3, 20000, 2000.0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() - 1 / 2000.0) < 0.03 / 2000.0        # exponential mean 1/rate
+    assert abs(gaps.std() - 1 / 2000.0) < 0.05 / 2000.0          # and standard deviation 1/rate
+    assert e.min() >= 16 and e.max() <= 96
+    assert abs(np.median(np.log(e)) - 0.5 * np.log(16 * 96)) < 0.05

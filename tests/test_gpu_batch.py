@@ -1,0 +1,225 @@
+"""Batched and served solves on the GPU, through the C ABI (cg_batch_*).
+
+Every system of a batch is checked against the oracle like a single solve
+(true residual <= tol, solution within 1e-8 of the oracle run for the same
+number of steps, stopping step within max(2, 1%) of the oracle's).  The batch
+machinery itself is checked by properties that hold for any correct runtime:
+a system gives the same bits alone and in any mix, in one launch or over
+many rounds (its state carried between launches), with one CTA or a group of
+CTAs within tolerance of each other; admission respects the memory budget;
+malformed and oversized requests are refused without disturbing the rest.
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+import oracle
+from gpu_util import cg_mod, iters_close, kappa_estimate
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _system(N, seed, kind="q1"):
+    A = fi.q1(N, 1.0, seed) if kind == "q1" else fi.laplace7(N)
+    xs = fi.xstar(seed, A.n)
+    b = oracle.spmv(A, xs)
+    return A, b
+
+
+def _request(A, b, host=True, tag=0, tol=TOL, maxit=None):
+    import torch
+    cg = cg_mod()
+    if host:
+        rp, ci, va = A.row_ptr.astype(np.int32), A.col_idx.astype(np.int32), A.val.astype(np.float64)
+        bb, x = b.copy(), np.zeros(A.n)
+    else:
+        rp, ci, va = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A.row_ptr, A.col_idx, A.val))
+        bb, x = torch.from_numpy(b).cuda(), torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    return cg.Request(rp, ci, va, bb, x, tol=tol, maxit=maxit, index_base=getattr(A, "index_base", 0), tag=tag)
+
+
+def _x(req):
+    x = req.x
+    return x.cpu().numpy() if hasattr(x, "cpu") else x
+
+
+def _check_vs_oracle(A, b, res, x):
+    cg = cg_mod()
+    assert res.done and res.status == cg.CG_OK, res
+    assert res.relres <= TOL
+    # the true residual recomputed by the oracle's product
+    tr = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert tr <= 1.0000001 * TOL
+    ref = oracle.cg(A, b, tol=TOL, maxit=10 * A.n)
+    assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+
+
+def test_batch_matches_oracle_per_system():
+    cg = cg_mod()
+    systems = [_system(N, 10 + N) for N in (2, 3, 5, 8, 12)] + [_system(6, 0, "lap")]
+    with cg.Batch() as bt:
+        reqs = [_request(A, b, host=(i % 2 == 0), tag=i) for i, (A, b) in enumerate(systems)]
+        tickets = bt.submit(reqs)
+        results = bt.wait_all(tickets)
+        st = bt.stats()
+    assert st["graph"] == 1, "rounds should replay a captured CUDA graph"
+    for (A, b), req, res in zip(systems, reqs, results):
+        assert res.tag == req.tag
+        _check_vs_oracle(A, b, res, _x(req))
+
+
+def test_alone_and_in_a_mix_give_the_same_bits():
+    cg = cg_mod()
+    A, b = _system(10, 77)
+    others = [_system(N, 200 + N) for N in (4, 7, 9, 13, 6)]
+    with cg.Batch() as bt:
+        r_alone = _request(A, b)
+        t = bt.submit([r_alone])[0]
+        ra = bt.wait(t)
+        mix = [_request(*s) for s in others[:2]] + [_request(A, b)] + [_request(*s) for s in others[2:]]
+        tm = bt.submit(mix)
+        rm = bt.wait_all(tm)
+    assert ra.status == cg.CG_OK and rm[2].status == cg.CG_OK
+    assert ra.iters == rm[2].iters
+    assert np.array_equal(_x(r_alone), _x(mix[2]))
+
+
+def test_rounds_resume_exactly():
+    """Advancing every system a few steps per launch (state saved and
+    reloaded between launches) gives the bits of one launch per system."""
+    cg = cg_mod()
+    systems = [_system(N, 300 + N) for N in (5, 9, 11)]
+    outs = {}
+    for chunk in (0, 7):
+        with cg.Batch(chunk_iters=chunk) as bt:
+            reqs = [_request(A, b) for A, b in systems]
+            res = bt.wait_all(bt.submit(reqs))
+            outs[chunk] = (reqs, res, bt.stats())
+    (r0, s0, st0), (r7, s7, st7) = outs[0], outs[7]
+    assert st7["rounds"] > st0["rounds"]
+    for a, b_, ra, rb in zip(r0, r7, s0, s7):
+        assert ra.status == rb.status == cg.CG_OK
+        assert ra.iters == rb.iters
+        assert rb.rounds >= ra.iters // 7
+        assert np.array_equal(_x(a), _x(b_))
+
+
+@pytest.mark.parametrize("group", [2, 5])
+def test_groups_of_ctas(group):
+    """A system shared by a group of CTAs (own group barrier, per-group sums)."""
+    cg = cg_mod()
+    systems = [_system(14, 400), _system(17, 401), _system(6, 402)]
+    with cg.Batch(group_override=group) as bt:
+        reqs = [_request(A, b) for A, b in systems]
+        res = bt.wait_all(bt.submit(reqs))
+    for (A, b), req, r in zip(systems, reqs, res):
+        assert r.group == group
+        _check_vs_oracle(A, b, r, _x(req))
+
+
+def test_groups_with_chunks_resume_exactly():
+    cg = cg_mod()
+    A, b = _system(15, 500)
+    xs = []
+    for chunk in (0, 5):
+        with cg.Batch(group_override=3, chunk_iters=chunk) as bt:
+            req = _request(A, b)
+            r = bt.wait(bt.submit([req])[0])
+            assert r.status == cg.CG_OK
+            xs.append((_x(req).copy(), r.iters))
+    assert xs[0][1] == xs[1][1] and np.array_equal(xs[0][0], xs[1][0])
+
+
+def test_budget_admission_and_release():
+    """A budget that holds about two systems at a time: every request still
+    completes, in rounds, and the arena never exceeds the budget."""
+    cg = cg_mod()
+    systems = [_system(12, 600 + i) for i in range(6)]
+    A0 = systems[0][0]
+    per = 12 * A0.nnz + 4 * A0.nnz + 80 * A0.n + 64 * 1024
+    with cg.Batch(budget_bytes=int(2.2 * per), chunk_iters=20) as bt:
+        reqs = [_request(A, b) for A, b in systems]
+        res = bt.wait_all(bt.submit(reqs))
+        st = bt.stats()
+    assert st["bytes_peak"] <= st["budget_bytes"]
+    assert st["bytes_in_use"] == 0 and st["resident"] == 0 and st["pending"] == 0
+    for (A, b), req, r in zip(systems, reqs, res):
+        _check_vs_oracle(A, b, r, _x(req))
+    # admission waited for memory: some request was admitted after another finished
+    assert max(r.admit_ms for r in res) >= min(r.done_ms for r in res)
+
+
+def test_oversized_and_malformed_requests():
+    cg = cg_mod()
+    A, b = _system(8, 700)
+    with cg.Batch(budget_bytes=1 << 20) as bt:
+        big = _request(*_system(20, 701))
+        with pytest.raises(cg.CGError) as e:
+            bt.submit([big])
+        assert e.value.status == cg.CG_ENOMEM
+        bad = _request(A, b)
+        bad.col_idx = bad.col_idx.copy()
+        bad.col_idx[5] = A.n + 3          # column out of range
+        good = _request(*_system(3, 702))
+        t_bad, t_good = bt.submit([bad, good])
+        r_bad, r_good = bt.wait(t_bad), bt.wait(t_good)
+    assert r_bad.done and r_bad.status == cg.CG_EINVAL
+    assert r_good.status == cg.CG_OK and r_good.relres <= TOL
+
+
+def test_empty_system_and_zero_rhs():
+    cg = cg_mod()
+    A, _ = _system(4, 800)
+    empty = fi.CSR(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0), 0)
+    with cg.Batch() as bt:
+        r_empty = _request(empty, np.zeros(0))
+        r_zero = _request(A, np.zeros(A.n))
+        r_zero.x[:] = 5.0  # overwritten: x0 = 0 and b = 0 give x = 0
+        res = bt.wait_all(bt.submit([r_empty, r_zero]))
+    assert res[0].status == cg.CG_OK and res[0].iters == 0
+    assert res[1].status == cg.CG_OK and res[1].iters == 0 and np.all(_x(r_zero) == 0.0)
+
+
+def test_mixed_precision_batch():
+    cg = cg_mod()
+    systems = [_system(N, 900 + N) for N in (6, 10, 16)]
+    with cg.Batch(precision=cg.CG_PREC_MIXED) as bt:
+        reqs = [_request(A, b) for A, b in systems]
+        res = bt.wait_all(bt.submit(reqs))
+    for (A, b), req, r in zip(systems, reqs, res):
+        assert r.status == cg.CG_OK and r.relres <= TOL
+        x = _x(req)
+        assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1.0000001 * TOL
+        ref = oracle.cg_mixed(A, b, tol=TOL)
+        assert ref.status == oracle.OK
+        # both are within kappa * 1e-10 of the exact solution
+        kap = kappa_estimate(A, b)
+        assert np.linalg.norm(x - ref.x) <= 2.0 * kap * TOL * np.linalg.norm(ref.x)
+
+
+def test_batch_of_256_uneven_systems_sampled():
+    """The 256-system workload (edges uniform in [8, 48], own densities and
+    right-hand side per system) in one batch: every system converges; a
+    sample is checked against the oracle's product."""
+    cg = cg_mod()
+    edges = fi.batch_edges(0, 256)
+    reqs, systems = [], []
+    for i, N in enumerate(edges):
+        sd = fi.system_seed(0, i)
+        A = fi.q1(int(N), 1.0, sd)
+        b = oracle.spmv(A, fi.xstar(sd, A.n))
+        systems.append((A, b))
+        reqs.append(_request(A, b, tag=i))
+    with cg.Batch(precision=cg.CG_PREC_MIXED) as bt:
+        res = bt.wait_all(bt.submit(reqs))
+        st = bt.stats()
+    assert st["completed"] == 256
+    assert all(r.status == cg.CG_OK and r.relres <= TOL for r in res)
+    for i in range(0, 256, 37):
+        A, b = systems[i]
+        x = _x(reqs[i])
+        assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1.0000001 * TOL
