@@ -40,6 +40,16 @@ def _request(A, b, host=True, tag=0, tol=TOL, maxit=None):
     return cg.Request(rp, ci, va, bb, x, tol=tol, maxit=maxit, index_base=getattr(A, "index_base", 0), tag=tag)
 
 
+def _wait_all(bt, tickets, limit_ms=120000):
+    res = bt.wait_all(tickets, limit_ms)
+    assert all(r.done for r in res), "a request did not finish within the limit"
+    return res
+
+
+def _wait1(bt, ticket, limit_ms=120000):
+    return _wait_all(bt, [ticket], limit_ms)[0]
+
+
 def _x(req):
     x = req.x
     return x.cpu().numpy() if hasattr(x, "cpu") else x
@@ -64,7 +74,7 @@ def test_batch_matches_oracle_per_system():
     with cg.Batch() as bt:
         reqs = [_request(A, b, host=(i % 2 == 0), tag=i) for i, (A, b) in enumerate(systems)]
         tickets = bt.submit(reqs)
-        results = bt.wait_all(tickets)
+        results = _wait_all(bt, tickets)
         st = bt.stats()
     assert st["graph"] == 1, "rounds should replay a captured CUDA graph"
     for (A, b), req, res in zip(systems, reqs, results):
@@ -79,10 +89,10 @@ def test_alone_and_in_a_mix_give_the_same_bits():
     with cg.Batch() as bt:
         r_alone = _request(A, b)
         t = bt.submit([r_alone])[0]
-        ra = bt.wait(t)
+        ra = _wait1(bt, t)
         mix = [_request(*s) for s in others[:2]] + [_request(A, b)] + [_request(*s) for s in others[2:]]
         tm = bt.submit(mix)
-        rm = bt.wait_all(tm)
+        rm = _wait_all(bt, tm)
     assert ra.status == cg.CG_OK and rm[2].status == cg.CG_OK
     assert ra.iters == rm[2].iters
     assert np.array_equal(_x(r_alone), _x(mix[2]))
@@ -97,7 +107,7 @@ def test_rounds_resume_exactly():
     for chunk in (0, 7):
         with cg.Batch(chunk_iters=chunk) as bt:
             reqs = [_request(A, b) for A, b in systems]
-            res = bt.wait_all(bt.submit(reqs))
+            res = _wait_all(bt, bt.submit(reqs))
             outs[chunk] = (reqs, res, bt.stats())
     (r0, s0, st0), (r7, s7, st7) = outs[0], outs[7]
     assert st7["rounds"] > st0["rounds"]
@@ -115,7 +125,7 @@ def test_groups_of_ctas(group):
     systems = [_system(14, 400), _system(17, 401), _system(6, 402)]
     with cg.Batch(group_override=group) as bt:
         reqs = [_request(A, b) for A, b in systems]
-        res = bt.wait_all(bt.submit(reqs))
+        res = _wait_all(bt, bt.submit(reqs))
     for (A, b), req, r in zip(systems, reqs, res):
         assert r.group == group
         _check_vs_oracle(A, b, r, _x(req))
@@ -128,7 +138,7 @@ def test_groups_with_chunks_resume_exactly():
     for chunk in (0, 5):
         with cg.Batch(group_override=3, chunk_iters=chunk) as bt:
             req = _request(A, b)
-            r = bt.wait(bt.submit([req])[0])
+            r = _wait1(bt, bt.submit([req])[0])
             assert r.status == cg.CG_OK
             xs.append((_x(req).copy(), r.iters))
     assert xs[0][1] == xs[1][1] and np.array_equal(xs[0][0], xs[1][0])
@@ -143,7 +153,7 @@ def test_budget_admission_and_release():
     per = 12 * A0.nnz + 4 * A0.nnz + 80 * A0.n + 64 * 1024
     with cg.Batch(budget_bytes=int(2.2 * per), chunk_iters=20) as bt:
         reqs = [_request(A, b) for A, b in systems]
-        res = bt.wait_all(bt.submit(reqs))
+        res = _wait_all(bt, bt.submit(reqs))
         st = bt.stats()
     assert st["bytes_peak"] <= st["budget_bytes"]
     assert st["bytes_in_use"] == 0 and st["resident"] == 0 and st["pending"] == 0
@@ -166,7 +176,7 @@ def test_oversized_and_malformed_requests():
         bad.col_idx[5] = A.n + 3          # column out of range
         good = _request(*_system(3, 702))
         t_bad, t_good = bt.submit([bad, good])
-        r_bad, r_good = bt.wait(t_bad), bt.wait(t_good)
+        r_bad, r_good = _wait1(bt, t_bad), _wait1(bt, t_good)
     assert r_bad.done and r_bad.status == cg.CG_EINVAL
     assert r_good.status == cg.CG_OK and r_good.relres <= TOL
 
@@ -179,7 +189,7 @@ def test_empty_system_and_zero_rhs():
         r_empty = _request(empty, np.zeros(0))
         r_zero = _request(A, np.zeros(A.n))
         r_zero.x[:] = 5.0  # overwritten: x0 = 0 and b = 0 give x = 0
-        res = bt.wait_all(bt.submit([r_empty, r_zero]))
+        res = _wait_all(bt, bt.submit([r_empty, r_zero]))
     assert res[0].status == cg.CG_OK and res[0].iters == 0
     assert res[1].status == cg.CG_OK and res[1].iters == 0 and np.all(_x(r_zero) == 0.0)
 
@@ -189,7 +199,7 @@ def test_mixed_precision_batch():
     systems = [_system(N, 900 + N) for N in (6, 10, 16)]
     with cg.Batch(precision=cg.CG_PREC_MIXED) as bt:
         reqs = [_request(A, b) for A, b in systems]
-        res = bt.wait_all(bt.submit(reqs))
+        res = _wait_all(bt, bt.submit(reqs))
     for (A, b), req, r in zip(systems, reqs, res):
         assert r.status == cg.CG_OK and r.relres <= TOL
         x = _x(req)
@@ -215,7 +225,7 @@ def test_batch_of_256_uneven_systems_sampled():
         systems.append((A, b))
         reqs.append(_request(A, b, tag=i))
     with cg.Batch(precision=cg.CG_PREC_MIXED) as bt:
-        res = bt.wait_all(bt.submit(reqs))
+        res = _wait_all(bt, bt.submit(reqs))
         st = bt.stats()
     assert st["completed"] == 256
     assert all(r.status == cg.CG_OK and r.relres <= TOL for r in res)
