@@ -479,9 +479,19 @@ void admit(cg_batch_ctx* b) {
   }
 }
 
-// Build the task queue of a round: groups of several CTAs first (largest
-// remaining work first, as many as fit in the grid at once), then one-CTA
-// systems, largest remaining work first.  Returns the systems of the round.
+// Build the task queue of a round: the ranks of every group of several CTAs
+// first (largest remaining work first), then one-CTA systems, largest
+// remaining work first.  Returns the systems of the round.
+//
+// CTAs take entries in queue order, so a group whose ranks do not all fit in
+// the first wave is completed by CTAs that finish earlier group tasks; its
+// first ranks wait at their first group barrier meanwhile.  This cannot
+// deadlock: take the first group in queue order with an entry not yet taken;
+// every entry before it has been taken, no entry after it has, so every busy
+// CTA outside that group runs a task that can finish (a one-CTA task or a
+// group whose ranks are all running), and each group has at most as many
+// ranks as the grid has CTAs.  Since groups precede one-CTA tasks, such waits
+// last at most as long as a group task.
 std::vector<Job*> build_queue(cg_batch_ctx* b, const std::vector<Job*>& res) {
   std::vector<Job*> groups, singles;
   for (Job* j : res) (j->group > 1 ? groups : singles).push_back(j);
@@ -497,10 +507,11 @@ std::vector<Job*> build_queue(cg_batch_ctx* b, const std::vector<Job*>& res) {
   std::sort(groups.begin(), groups.end(), by_work);
   std::sort(singles.begin(), singles.end(), by_work);
   std::vector<Job*> in_round;
-  int nt = 0, ctas = 0;
+  int nt = 0;
+  int room = b->task_cap - static_cast<int>(singles.size());
   for (Job* j : groups) {
-    if (ctas + j->group > b->nblocks) continue;  // next round
-    ctas += j->group;
+    if (j->group > room) continue;  // the queue is full: next round
+    room -= j->group;
     for (int rk = 0; rk < j->group; ++rk) b->h_queue->task[nt++] = cgk::BatchTask{j->slot, rk};
     in_round.push_back(j);
   }
@@ -707,7 +718,9 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   }
   b->nblocks = sms * per_sm;
   b->model.cta_rate = 6.7e12 / b->nblocks;
-  b->task_cap = b->max_systems + b->nblocks;
+  // queue capacity: every resident system once, plus the extra ranks of
+  // groups (a round whose groups need more is split over rounds)
+  b->task_cap = 2 * b->max_systems + 8 * b->nblocks;
   b->queue_bytes = sizeof(cgk::BatchQueue) + sizeof(cgk::BatchTask) * (b->task_cap - 1);
 
   size_t budget = static_cast<size_t>(o.budget_bytes);

@@ -233,3 +233,19 @@ def test_batch_of_256_uneven_systems_sampled():
         A, b = systems[i]
         x = _x(reqs[i])
         assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1.0000001 * TOL
+
+
+def test_groups_beyond_one_wave():
+    """More group ranks than the grid has CTAs: later groups are taken by
+    CTAs that finish earlier group tasks (in one launch), and every system
+    still matches the oracle."""
+    cg = cg_mod()
+    systems = [_system(13 + i, 1000 + i) for i in range(4)]
+    with cg.Batch(group_override=100) as bt:
+        reqs = [_request(A, b) for A, b in systems]
+        res = _wait_all(bt, bt.submit(reqs))
+        st = bt.stats()
+    assert st["rounds"] == 1
+    for (A, b), req, r in zip(systems, reqs, res):
+        assert r.group == min(100, st["nblocks"])
+        _check_vs_oracle(A, b, r, _x(req))
