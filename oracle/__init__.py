@@ -63,6 +63,10 @@ def _bind(lib):
     lib.oracle_spmv_f32.argtypes = [i64, vp, vp, vp, ci, vp, vp]
     lib.oracle_cg_mixed.restype = ci
     lib.oracle_cg_mixed.argtypes = [i64, vp, vp, vp, vp, ci, vp, vp, dbl, i64, i64, vp, vp, vp]
+    lib.oracle_jacobi_dinv.restype = ci
+    lib.oracle_jacobi_dinv.argtypes = [i64, vp, vp, vp, ci, vp]
+    lib.oracle_pcg_jacobi.restype = ci
+    lib.oracle_pcg_jacobi.argtypes = [i64, vp, vp, vp, ci, vp, vp, dbl, i64, i64, vp, vp, vp]
     lib.oracle_matrix_stats.restype = None
     lib.oracle_matrix_stats.argtypes = [i64, vp, vp, ci, vp]
     return lib
@@ -199,6 +203,28 @@ def cg_mixed(A, b, tol: float = 1e-10, maxit: int | None = None, replace_every: 
     st = _load().oracle_cg_mixed(n, _p(rp), _p(ci), _p(va), _p(v32), int(getattr(A, "index_base", 0)),
                                  _p(b), _p(x), float(tol), int(maxit), int(replace_every),
                                  ctypes.byref(it), ctypes.byref(rr), ctypes.byref(rt))
+    return CGResult(x, st, it.value, rr.value, rt.value)
+
+
+def jacobi_dinv(A):
+    """1 / diag(A), or None if a diagonal entry is not positive."""
+    rp, ci, va = _i32(A.row_ptr), _i32(A.col_idx), _f64(A.val)
+    out = np.zeros(A.n)
+    st = _load().oracle_jacobi_dinv(A.n, _p(rp), _p(ci), _p(va), int(getattr(A, "index_base", 0)), _p(out))
+    return out if st == OK else None
+
+
+def pcg_jacobi(A, b, tol: float = 1e-10, maxit: int | None = None, x0=None, force_iters: int = -1) -> CGResult:
+    """Jacobi-preconditioned CG (M = diag(A)); ``force_iters >= 0`` runs exactly that many steps."""
+    n = A.n
+    rp, ci, va, b = _i32(A.row_ptr), _i32(A.col_idx), _f64(A.val), _f64(b)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    maxit = n if maxit is None else maxit
+    it = ctypes.c_int64(0)
+    rr, rt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = _load().oracle_pcg_jacobi(n, _p(rp), _p(ci), _p(va), int(getattr(A, "index_base", 0)), _p(b), _p(x),
+                                   float(tol), int(maxit), int(force_iters), ctypes.byref(it), ctypes.byref(rr),
+                                   ctypes.byref(rt))
     return CGResult(x, st, it.value, rr.value, rt.value)
 
 

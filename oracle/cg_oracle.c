@@ -18,6 +18,8 @@
  *                 the paper prints no listing and cites Saad, "Iterative
  *                 Methods for Sparse Linear Systems" — the Hestenes-Stiefel form
  *                 is followed step by step.
+ *   oracle_pcg_jacobi  preconditioned CG with M = diag(A) (z = dinv .* r by
+ *                 the element-wise product), and oracle_jacobi_dinv.
  *   oracle_spmv_f32 / oracle_cg_mixed   the mixed-precision variant (FP32
  *                 matrix values and FP32-accumulated product; FP64 dots,
  *                 scalars, x and a true-residual replacement every k steps),
@@ -231,6 +233,97 @@ int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const doubl
     for (int64_t i = 0; i < n; ++i) { double d = b[i] - q[i]; t = t + d * d; }
     *relres_true = sqrt(t) / bnorm;
     free(r); free(p); free(q); free(p32); free(q32);
+    return status;
+}
+
+/* ---------------------------------------------------------------- Jacobi */
+
+/* Inverse of the diagonal of A: dinv[i] = 1 / (sum of the stored entries of
+ * row i in column i).  Returns 0, or ORC_BREAKDOWN if some diagonal is not
+ * positive (then A is not SPD and no Jacobi preconditioner exists). */
+int oracle_jacobi_dinv(int64_t n, const int32_t* IA, const int32_t* JA, const double* AA, int base,
+                       double* dinv) {
+    for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int64_t k = (int64_t)IA[i] - base; k < (int64_t)IA[i + 1] - base; ++k)
+            if ((int64_t)JA[k] - base == i) d = d + AA[k];
+        if (!(d > 0.0)) return ORC_BREAKDOWN;
+        dinv[i] = 1.0 / d;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Jacobi-preconditioned CG: the preconditioned conjugate gradient iteration
+ * with M = diag(A), the preconditioner applied as the element-wise product
+ * z = dinv .* r (the paper's Sec. 5.2 element-wise product; it defers
+ * preconditioning itself to domain decomposition):
+ *   r = b - A x;  z = dinv .* r;  p = z;  rho = r.z
+ *   for k = 1..maxit:
+ *     q = A p;  gamma = p.q   (gamma <= 0 or not finite -> breakdown)
+ *     alpha = rho / gamma;  x = x + alpha p;  r = r - alpha q
+ *     if ||r|| <= tol*||b||: stop with k iterations   (the unpreconditioned test)
+ *     z = dinv .* r;  rho_new = r.z;  beta = rho_new / rho;  p = z + beta p;  rho = rho_new
+ * force_iters >= 0 runs exactly that many steps.  A diagonal that is not
+ * positive gives ORC_BREAKDOWN with x untouched.
+ */
+int oracle_pcg_jacobi(int64_t n, const int32_t* IA, const int32_t* JA, const double* AA, int base,
+                      const double* b, double* x, double tol, int64_t maxit, int64_t force_iters,
+                      int64_t* iters, double* relres_rec, double* relres_true) {
+    size_t m = (size_t)(n > 0 ? n : 1);
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* z = (double*)malloc(sizeof(double) * m);
+    double* p = (double*)malloc(sizeof(double) * m);
+    double* q = (double*)malloc(sizeof(double) * m);
+    double* dinv = (double*)malloc(sizeof(double) * m);
+    if (!r || !z || !p || !q || !dinv) { free(r); free(z); free(p); free(q); free(dinv); return ORC_NOMEM; }
+    *iters = 0;
+    *relres_rec = 0.0;
+    *relres_true = 0.0;
+    if (oracle_jacobi_dinv(n, IA, JA, AA, base, dinv) != ORC_OK) {
+        free(r); free(z); free(p); free(q); free(dinv);
+        return ORC_BREAKDOWN;
+    }
+    int status = ORC_OK;
+    double bnorm = sqrt(oracle_dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        free(r); free(z); free(p); free(q); free(dinv);
+        return ORC_OK;
+    }
+    oracle_spmv(n, IA, JA, AA, base, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    oracle_ewmul(n, dinv, r, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    double rho = oracle_dot(n, r, z);
+    double rr = oracle_dot(n, r, r);
+    int64_t k = 0;
+    int done = (force_iters < 0) && (sqrt(rr) <= tol * bnorm);
+    int64_t limit = force_iters >= 0 ? force_iters : maxit;
+    while (!done && k < limit) {
+        oracle_spmv(n, IA, JA, AA, base, p, q);
+        double gamma = oracle_dot(n, p, q);
+        if (!(gamma > 0.0) || !isfinite(gamma)) { status = ORC_BREAKDOWN; break; }
+        double alpha = rho / gamma;
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+        rr = oracle_dot(n, r, r);
+        k = k + 1;
+        if (force_iters < 0 && sqrt(rr) <= tol * bnorm) { done = 1; break; }
+        oracle_ewmul(n, dinv, r, z);
+        double rho_new = oracle_dot(n, r, z);
+        double beta = rho_new / rho;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rho = rho_new;
+    }
+    *iters = k;
+    *relres_rec = sqrt(rr) / bnorm;
+    if (status == ORC_OK && force_iters < 0 && !done) status = ORC_NOTCONV;
+    oracle_spmv(n, IA, JA, AA, base, x, q);
+    double t = 0.0;
+    for (int64_t i = 0; i < n; ++i) { double d = b[i] - q[i]; t = t + d * d; }
+    *relres_true = sqrt(t) / bnorm;
+    free(r); free(z); free(p); free(q); free(dinv);
     return status;
 }
 

@@ -279,6 +279,50 @@ def pin_matrix_stats(golden_table1=True):
     assert abs(sq["nz_per_h_stddev"] - float(np.std(L))) <= 1e-12
 
 
+def pin_pcg_jacobi():
+    """Jacobi-preconditioned CG against facts outside it.
+    (1) Symmetric scaling: with D = diag(A), PCG's iterates are D^(-1/2) times
+        those of plain CG on D^(-1/2) A D^(-1/2) with right-hand side
+        D^(-1/2) b (the textbook equivalence), step by step.
+    (2) A diagonal matrix is its own preconditioner: one step gives the exact
+        solution.
+    (3) A constant diagonal (the 7-point operator, diagonal 6) makes the
+        preconditioner a multiple of the identity: the iterates are CG's.
+    (4) The inverse diagonal is the reciprocal of the brute-force diagonal;
+        a non-positive diagonal is refused (breakdown)."""
+    A = fi.q1(5, sigma=1.0, seed=31)
+    D = A.to_dense()
+    d = np.diag(D).copy()
+    dinv = oracle.jacobi_dinv(A)
+    assert dinv is not None and np.allclose(dinv, 1.0 / d, rtol=1e-15, atol=0)
+    s = 1.0 / np.sqrt(d)
+    As = fi.dense_to_csr(D * s[:, None] * s[None, :])
+    b = D @ fi.xstar(31, A.n)
+    for k in (1, 2, 3, 5, 8, 13):
+        xp = oracle.pcg_jacobi(A, b, tol=0.0, maxit=k, force_iters=k).x
+        xh = oracle.cg(As, s * b, tol=0.0, maxit=k, force_iters=k).x
+        assert np.linalg.norm(xp - s * xh) <= 1e-10 * np.linalg.norm(xp), k
+    r = oracle.pcg_jacobi(A, b, tol=1e-10, maxit=10 * A.n)
+    assert r.status == oracle.OK and r.relres_true <= 1e-10 * 1.0000001
+    xd = np.linalg.solve(D, b)
+    assert np.linalg.norm(r.x - xd) <= 2 * np.linalg.cond(D) * 1e-10 * np.linalg.norm(xd)
+    # (2)
+    Dg = fi.dense_to_csr(np.diag(np.arange(1.0, 9.0)))
+    bg = np.arange(1.0, 9.0) ** 2
+    r = oracle.pcg_jacobi(Dg, bg, tol=1e-14, maxit=10)
+    assert r.iters == 1 and np.allclose(r.x, np.arange(1.0, 9.0), rtol=1e-15)
+    # (3)
+    L = fi.laplace7(6)
+    bl = oracle.spmv(L, fi.xstar(32, L.n))
+    rp, rc = oracle.pcg_jacobi(L, bl, tol=1e-10, maxit=1000), oracle.cg(L, bl, tol=1e-10, maxit=1000)
+    assert abs(rp.iters - rc.iters) <= 1
+    assert np.linalg.norm(rp.x - rc.x) <= 1e-9 * np.linalg.norm(rc.x)
+    # (4)
+    Bad = fi.dense_to_csr(np.array([[2.0, 0.5], [0.5, -1.0]]))
+    assert oracle.jacobi_dinv(Bad) is None
+    assert oracle.pcg_jacobi(Bad, np.ones(2)).status == oracle.BREAKDOWN
+
+
 ALL_PINS = [
     pin_spmv_paper_example,
     pin_spmv_dense_bruteforce,
@@ -291,5 +335,6 @@ ALL_PINS = [
     pin_cg_orthogonality,
     pin_cg_special_cases,
     pin_mixed_cg,
+    pin_pcg_jacobi,
     pin_matrix_stats,
 ]

@@ -39,6 +39,13 @@ MUTANTS = [
     ("mixed_beta_from_true_residual",
      "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
      "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n            beta = rho_new / rho;\n        }"),
+    ("pcg_no_preconditioner", "oracle_ewmul(n, dinv, r, z);\n        double rho_new = oracle_dot(n, r, z);",
+     "for (int64_t i = 0; i < n; ++i) z[i] = r[i];\n        double rho_new = oracle_dot(n, r, z);"),
+    ("pcg_rho_uses_r_r", "double rho_new = oracle_dot(n, r, z);", "double rho_new = oracle_dot(n, r, r);"),
+    ("pcg_direction_from_r", "for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];",
+     "for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];"),
+    ("jacobi_diag_from_first_entry", "if ((int64_t)JA[k] - base == i) d = d + AA[k];",
+     "if (k == (int64_t)IA[i] - base) d = d + AA[k];"),
     ("stats_bandwidth_off_by_one", "int64_t d = (int64_t)(JA[k] - base) - i;", "int64_t d = (int64_t)(JA[k] - base) - i + 1;"),
 ]
 
