@@ -607,13 +607,20 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
       else tot = warp_sum_f(acc);
       if (lane == 0) epi(d0.x, tot, aux != nullptr ? aux[d0.x] : 0.0);
     } else {
-      const int wmax = (m0 >> kWmaxShift) & 0xff;
       int a, len;
       lane_span(r0, mode, a, len);
       const int p0 = pos(a);
-      X xv[kLaneMax];
-      seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
-      const Acc part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv);
+      Acc part;
+      if constexpr (kRingPass) {
+        const int wmax = (m0 >> kWmaxShift) & 0xff;
+        X xv[kLaneMax];
+        seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
+        part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv);
+      } else {
+        // the direct pass (rare: residual replacements) uses the compact
+        // loop: the same FMAs in the same order, far fewer registers
+        part = seg_dot_loop<T, X, Acc>(rv + p0, rc + p0, len, x);
+      }
       if (mode == kPairPerRow) {
         // first half + second half: the same value in both lanes (commutative add)
         const Acc sum = part + __shfl_xor_sync(0xffffffffu, part, 1);

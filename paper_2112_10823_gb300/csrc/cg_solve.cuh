@@ -104,14 +104,17 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     slot ^= 1;
     return true;
   };
-  // FP64 products: from the ring in the FP64 solve; read directly from
-  // global memory in the mixed solve (whose ring carries the FP32 values).
-  // Every product pass ends with a vote of all consumer warps, so that a warp
-  // that gave up on a wait and the others leave together.
+  // The products outside the step loop (setup, true residual at the end,
+  // and the mixed solve's residual replacements) read the FP64 values and
+  // columns directly from global memory with a compact per-lane loop: they
+  // run once per solve (or once every replace_every steps), and keeping the
+  // large unrolled ring product out of them leaves its single copy, in the
+  // step loop, the registers it needs.  The ring keeps streaming the values
+  // the step loop uses.  Every product pass ends with a vote of all consumer
+  // warps, so that a warp that gave up on a wait and the others leave
+  // together.
   auto product64 = [&](const double* xin, const double* aux, auto& epi) -> bool {
-    bool ok;
-    if constexpr (kMixed) ok = spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
-    else ok = spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
+    const bool ok = spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
     return cta_and(ok);
   };
 
