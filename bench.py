@@ -72,6 +72,8 @@ def parse(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the arrival window")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="device memory budget of the server")
     ap.add_argument("--chunk", type=int, default=50, help="serve: steps per system per round")
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
+                    help="none: the paper's plain CG; jacobi: preconditioned by diag(A)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle work for cpu_baseline (and per reference-arm step on large systems)")
     return ap.parse_args(argv)
@@ -119,14 +121,17 @@ def replacements(iters: int, every: int) -> int:
     return iters // every + 1
 
 
-def solve_bytes(n: int, nnz: int, iters: int, mixed: bool, every: int = 50) -> int:
+def solve_bytes(n: int, nnz: int, iters: int, mixed: bool, every: int = 50, jacobi: bool = False) -> int:
+    """Algorithmic bytes of a solve; Jacobi adds the inverse diagonal, read
+    in the residual update and in the direction update (16 B per row)."""
+    extra = 16 * n * iters if jacobi else 0
     if not mixed:
-        return iters * algorithmic_bytes_per_iter(n, nnz)
-    return iters * mixed_bytes_per_iter(n, nnz) + replacements(iters, every) * replacement_bytes(n, nnz)
+        return iters * algorithmic_bytes_per_iter(n, nnz) + extra
+    return iters * mixed_bytes_per_iter(n, nnz) + replacements(iters, every) * replacement_bytes(n, nnz) + extra
 
 
-def solve_flops(n: int, nnz: int, iters: int, mixed: bool, every: int = 50) -> int:
-    f = iters * flops_per_iter(n, nnz)
+def solve_flops(n: int, nnz: int, iters: int, mixed: bool, every: int = 50, jacobi: bool = False) -> int:
+    f = iters * flops_per_iter(n, nnz) + (3 * n * iters if jacobi else 0)
     if mixed:
         f += replacements(iters, every) * (2 * nnz + 2 * n)
     return f
@@ -163,7 +168,7 @@ def recorded_traffic(kernel: str, workload: str):
         if not line.startswith("traffic "):
             continue
         kv = dict(tok.split("=", 1) for tok in line.split()[1:] if "=" in tok)
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha") == sha:
+        if kv.get("kernel") == kernel.replace(" ", "") and kv.get("workload") == workload and kv.get("source_sha") == sha:
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -314,24 +319,27 @@ def whole_job_rate(steps: int, world: int, t_max: float) -> float:
     return steps * world / t_max
 
 
-def workload_name(grid: int, precision: str) -> str:
+def workload_name(grid: int, precision: str, precond: str = "none") -> str:
     prec = "FP64 CSR" if precision == "fp64" else "FP32-value product with FP64 residual replacement every 50 steps"
-    return f"Q1 27-point FE, {grid}^3 grid, lognormal rho (sigma=1), {prec}, CG to 1e-10"
+    method = "CG" if precond == "none" else "Jacobi-preconditioned CG"
+    return f"Q1 27-point FE, {grid}^3 grid, lognormal rho (sigma=1), {prec}, {method} to 1e-10"
 
 
-def oracle_solver(precision: str):
+def oracle_solver(precision: str, precond: str = "none"):
     import oracle
+    if precond == "jacobi":
+        return lambda A, b, maxit: oracle.pcg_jacobi(A, b, tol=TOL, maxit=maxit)
     if precision == "mixed":
         return lambda A, b, maxit: oracle.cg_mixed(A, b, tol=TOL, maxit=maxit)
     return lambda A, b, maxit: oracle.cg(A, b, tol=TOL, maxit=maxit)
 
 
-def oracle_rate(A, b, precision: str, budget_s: float, iters_full: int):
+def oracle_rate(A, b, precision: str, budget_s: float, iters_full: int, precond: str = "none"):
     """The oracle's solves/s on one host core: whole solves when one takes
     less than half the budget, else runs of 20 steps (each with its setup
     product) whose time per step is scaled to an `iters_full`-step solve.
     Returns (solves/s, description of the sample)."""
-    solve = oracle_solver(precision)
+    solve = oracle_solver(precision, precond)
     m = 20
     t0 = time.perf_counter()
     solve(A, b, m)
@@ -372,13 +380,13 @@ def run_reference(args):
     for s in range(args.warmup + args.steps):
         if iters_hint is None:
             t0 = time.perf_counter()
-            r = oracle_solver(args.precision)(A, b, 10 * A.n)
+            r = oracle_solver(args.precision, args.precond)(A, b, 10 * A.n)
             dt = time.perf_counter() - t0
             iters = r.iters
             sample = f"{args.steps} full oracle solves of the workload (each step one solve, {iters} iterations)"
         else:
             iters = iters_hint
-            v, sample = oracle_rate(A, b, args.precision, args.cpu_budget / 4, iters_hint)
+            v, sample = oracle_rate(A, b, args.precision, args.cpu_budget / 4, iters_hint, args.precond)
             dt = 1.0 / v
             sample = "each step: " + sample
         if s >= args.warmup:
@@ -390,7 +398,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.grid, args.precision),
+        "config": {"workload": workload_name(args.grid, args.precision, args.precond),
                    "n": A.n, "nnz": A.nnz, "iters": iters, "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -418,7 +426,9 @@ def run_ours(args):
     ci = torch.from_numpy(A.col_idx).to(dev)
     va = torch.from_numpy(A.val).to(dev)
     mixed = args.precision == "mixed"
-    h = cg.cg_create(rp, ci, va, stream=stream, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64)
+    jac = args.precond == "jacobi"
+    h = cg.cg_create(rp, ci, va, stream=stream, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64,
+                     preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
     h64 = cg.cg_create(rp, ci, va, stream=stream) if mixed else None   # FP64 solve for the accuracy record
     del rp, ci, va
     xs_d = torch.from_numpy(xs).to(dev)
@@ -527,11 +537,11 @@ def run_ours(args):
 
     # ---- roofline of the solve kernel (one launch per solve)
     launch_s = dev_time / args.steps
-    bytes_launch = solve_bytes(n, nnz, iters, mixed)
-    flops_launch = solve_flops(n, nnz, iters, mixed)
+    bytes_launch = solve_bytes(n, nnz, iters, mixed, jacobi=jac)
+    flops_launch = solve_flops(n, nnz, iters, mixed, jacobi=jac)
     achieved_gbs = bytes_launch / launch_s / 1e9
     achieved_gflops = flops_launch / launch_s / 1e9
-    kname = f"cg_solve_kernel<{'true' if mixed else 'false'}>"
+    kname = f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>"
     traffic = recorded_traffic(kname, f"q1_{args.grid}")
     if l2_resident(n, nnz, mixed) or not mixed and achieved_gflops / FP64_PEAK_GFLOPS > achieved_gbs / hbm_peak:
         # the system stays in L2 during a solve (or the FP64 pipe is nearer its
@@ -553,13 +563,13 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         import oracle
         b_host = b.cpu().numpy()
-        v, sample = oracle_rate(A, b_host, args.precision, args.cpu_budget, iters)
+        v, sample = oracle_rate(A, b_host, args.precision, args.cpu_budget, iters, args.precond)
         base = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.grid, args.precision),
+        "config": {"workload": workload_name(args.grid, args.precision, args.precond),
                    "n": n, "nnz": nnz, "iters": iters, "tol": TOL, "x0": "zero",
                    "l2": "flushed before every timed solve (256 MiB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -658,8 +668,10 @@ def run_batch(args):
            "joules_per_solve": (j1 - j0) / (count * args.steps) if j0 is not None and j1 is not None else None,
            "launches_per_batch": count}
 
+    jac = args.precond == "jacobi"
     bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=0, validate=False,
-                  budget_bytes=int(args.budget_gb * 2**30), max_systems=max(1024, count))
+                  budget_bytes=int(args.budget_gb * 2**30), max_systems=max(1024, count),
+                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
 
     def step():
         reqs = [cg.Request(s["rp"], s["ci"], s["va"], s["b"], s["x"], tol=TOL, maxit=10 * s["n"], tag=i)
@@ -689,8 +701,8 @@ def run_batch(args):
     iters = [r.iters for r in res]
     groups = [r.group for r in res]
     err = max(float(torch.linalg.vector_norm(s["x"] - x) / torch.linalg.vector_norm(x)) for s, x in zip(systems, x64))
-    bytes_batch = sum(solve_bytes(s["n"], s["nnz"], it, mixed) for s, it in zip(systems, iters))
-    flops_batch = sum(solve_flops(s["n"], s["nnz"], it, mixed) for s, it in zip(systems, iters))
+    bytes_batch = sum(solve_bytes(s["n"], s["nnz"], it, mixed, jacobi=jac) for s, it in zip(systems, iters))
+    flops_batch = sum(solve_flops(s["n"], s["nnz"], it, mixed, jacobi=jac) for s, it in zip(systems, iters))
     per_round = dev_s / rounds
     achieved = bytes_batch * args.steps / dev_s / 1e9
     line = {
@@ -700,7 +712,7 @@ def run_batch(args):
         "config": {"workload": f"batch of {count} Q1 27-point FE systems, grid edges uniform in [8, 48], "
                                f"lognormal rho (sigma=1), own b per system, "
                                f"{'mixed precision' if mixed else 'FP64'}, one persistent launch per batch "
-                               f"(CUDA graph), CG to 1e-10",
+                               f"(CUDA graph), {'Jacobi-preconditioned ' if jac else ''}CG to 1e-10",
                    "systems": count, "sum_n": int(sum(s["n"] for s in systems)),
                    "sum_nnz": int(sum(s["nnz"] for s in systems)), "iters_min": min(iters), "iters_max": max(iters),
                    "groups": {str(g): groups.count(g) for g in sorted(set(groups))},
@@ -708,7 +720,7 @@ def run_batch(args):
                    "l2": "flushed before every step (256 MiB write); the batch's matrices exceed L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
-                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}>",
+                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>",
                      "gflops": flops_batch * args.steps / dev_s / 1e9, "round_ms": 1000.0 * per_round},
         "accuracy": {"max_relres_true": max(r.relres for r in res),
                      "max_rel_diff_vs_fp64_cg_solve": err},
@@ -852,7 +864,7 @@ def run_serve(args):
         "speedup_vs_fp64_fifo": value / fifo["solves_per_s"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
-                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}>",
+                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}, false>",
                      "device_busy_frac": dev_s / t_end},
         "energy": {"joules_per_solve": (j1 - j0) / count if j0 is not None and j1 is not None else None,
                    "fp64_fifo_joules_per_solve": None, "source": "NVML board energy over the whole stream"},

@@ -67,6 +67,14 @@ typedef enum {
                         r replaced by the FP64 true residual every replace_every steps */
 } cg_precision;
 
+/* Preconditioner of cg_solve (the paper's CG has none; it defers
+ * preconditioning to domain decomposition). */
+typedef enum {
+  CG_PRECOND_NONE = 0,   /* classical CG (default) */
+  CG_PRECOND_JACOBI = 1  /* M = diag(A): z = diag(A)^-1 r by the element-wise product;
+                            the stopping test stays ||r|| <= tol ||b|| */
+} cg_preconditioner;
+
 typedef struct {
   void* stream;           /* cudaStream_t for all work of the handle; NULL = legacy default stream */
   int32_t device;         /* CUDA device ordinal; -1 = the current device */
@@ -74,7 +82,8 @@ typedef struct {
   int32_t replace_every;  /* CG_PREC_MIXED: residual-replacement period in steps (default 50) */
   int32_t validate;       /* 1 (default): check the CSR in cg_create (O(n + nnz) on the host) */
   int32_t wait_limit_ms;  /* bound on any device-side wait inside a kernel (default 2000) */
-  int32_t reserved[7];    /* zero */
+  int32_t preconditioner; /* cg_preconditioner (default CG_PRECOND_NONE) */
+  int32_t reserved[6];    /* zero */
 } cg_opts;
 
 /* Fill *o with the defaults above. */
@@ -87,6 +96,9 @@ void cg_opts_default(cg_opts* o);
  * With validate = 1 it rejects (CG_EINVAL): index_base not 0/1, row_ptr[0]
  * != base, decreasing row_ptr, row_ptr[n] != nnz + base, a column outside
  * [base, n + base).  n = 0 is allowed (every call is then a no-op).
+ * With preconditioner = CG_PRECOND_JACOBI the inverse diagonal is computed
+ * on the device (each row's entries in its own column summed); a diagonal
+ * that is not positive (A cannot be SPD) is refused with CG_EINVAL.
  * opts may be NULL (defaults).  On failure *out is NULL.
  */
 int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const cg_opts* opts);
@@ -130,7 +142,8 @@ int cg_ewmul(cg_handle h, int64_t n, const double* x, const double* y, double* z
  *   r = b - A x0, p = r; each step q = A p, alpha = r.r / p.q,
  *   x += alpha p, r -= alpha q, beta = r'.r' / r.r, p = r' + beta p;
  *   stop when ||r|| <= tol ||b|| (recursive residual; in CG_PREC_MIXED the
- *   replaced, true residual).
+ *   replaced, true residual).  With CG_PRECOND_JACOBI: z = diag(A)^-1 r,
+ *   r.z in place of r.r in alpha and beta, p = z' + beta p; same test.
  * b (n doubles) and x (n doubles; in: initial guess, out: solution) may be
  * device or host pointers (each detected separately; host memory is copied
  * in and out inside the call).  One persistent cooperative kernel runs the
@@ -222,7 +235,9 @@ typedef struct {
   int32_t use_graph;       /* 1 (default): replay each round from a captured CUDA graph */
   int32_t group_override;  /* > 0: every system uses this many CTAs (tests); 0 = automatic */
   int32_t validate;        /* 1 (default): check each request's CSR on the host */
-  int32_t reserved[6];     /* zero */
+  int32_t preconditioner;  /* cg_preconditioner of every system (a non-positive diagonal
+                              ends that request with CG_EINVAL) */
+  int32_t reserved[5];     /* zero */
 } cg_batch_opts;
 
 /* One system to solve: A x = b from x0 = 0. */

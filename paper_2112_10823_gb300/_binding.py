@@ -18,6 +18,7 @@ CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ENOTCONV, CG_EBREAKDOWN, CG_ETIMEOUT, 
 STATUS_NAMES = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_ENOTCONV",
                 5: "CG_EBREAKDOWN", 6: "CG_ETIMEOUT", 7: "CG_EBUSY"}
 CG_PREC_FP64, CG_PREC_MIXED = 0, 1
+CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
 
 
 class CGError(RuntimeError):
@@ -34,7 +35,8 @@ class cg_csr(ctypes.Structure):
 class cg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("replace_every", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("wait_limit_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("wait_limit_ms", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class cg_batch_opts(ctypes.Structure):
@@ -43,7 +45,7 @@ class cg_batch_opts(ctypes.Structure):
                 ("replace_every", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
                 ("max_pending", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("group_override", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("preconditioner", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class cg_request(ctypes.Structure):
@@ -208,7 +210,8 @@ class Handle:
 
 def cg_create(row_ptr, col_idx, val, n: int | None = None, nnz: int | None = None, index_base: int = 0,
               stream=None, device: int | None = None, precision: int = CG_PREC_FP64,
-              replace_every: int = 50, validate: bool = True, wait_limit_ms: int = 2000) -> Handle:
+              replace_every: int = 50, validate: bool = True, wait_limit_ms: int = 2000,
+              preconditioner: int = CG_PRECOND_NONE) -> Handle:
     """cg_create: copy a CSR matrix (IA/JA/AA; host or CUDA arrays) to the GPU.
 
     ``stream``: a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int, or None for
@@ -244,6 +247,7 @@ def cg_create(row_ptr, col_idx, val, n: int | None = None, nnz: int | None = Non
     o.replace_every = int(replace_every)
     o.validate = 1 if validate else 0
     o.wait_limit_ms = int(wait_limit_ms)
+    o.preconditioner = int(preconditioner)
     out = ctypes.c_void_p(0)
     _check(lib.cg_create(ctypes.byref(out), ctypes.byref(csr), n, nnz, ctypes.byref(o)))
     return Handle(out.value, n, nnz, s)
@@ -387,13 +391,14 @@ class Batch:
     def __init__(self, precision: int = CG_PREC_FP64, budget_bytes: int = 0, max_systems: int = 1024,
                  chunk_iters: int = 0, replace_every: int = 50, wait_limit_ms: int = 2000,
                  max_pending: int = 65536, use_graph: bool = True, group_override: int = 0,
-                 validate: bool = True, device: int = -1):
+                 validate: bool = True, device: int = -1, preconditioner: int = CG_PRECOND_NONE):
         o = cg_batch_opts()
         lib.cg_batch_opts_default(ctypes.byref(o))
         o.device, o.precision, o.budget_bytes = int(device), int(precision), int(budget_bytes)
         o.max_systems, o.chunk_iters, o.replace_every = int(max_systems), int(chunk_iters), int(replace_every)
         o.wait_limit_ms, o.max_pending, o.use_graph = int(wait_limit_ms), int(max_pending), 1 if use_graph else 0
         o.group_override, o.validate = int(group_override), 1 if validate else 0
+        o.preconditioner = int(preconditioner)
         out = ctypes.c_void_p(0)
         st = lib.cg_batch_create(ctypes.byref(out), ctypes.byref(o))
         if st != CG_OK:

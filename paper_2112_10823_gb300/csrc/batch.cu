@@ -131,7 +131,7 @@ bool is_device_ptr(const void* p) {
 
 // Upper bound of a system's device footprint (before its partition is known:
 // at most one step per row).
-size_t footprint_bound(int64_t n, int64_t nnz, bool mixed, int nblocks) {
+size_t footprint_bound(int64_t n, int64_t nnz, bool mixed, bool jacobi, int nblocks) {
   const size_t pad = cgk::kPadEntries;
   size_t b = 0;
   b += align_up(4 * (n + 1));
@@ -139,7 +139,7 @@ size_t footprint_bound(int64_t n, int64_t nnz, bool mixed, int nblocks) {
   if (mixed) b += align_up(4 * (nnz + pad)) + align_up(4 * n);
   b += align_up(sizeof(int4) * (n + 2)) + align_up(4 * (n + 2));
   b += 2 * align_up(4 * (static_cast<size_t>(nblocks) + 1));
-  b += 5 * align_up(8 * n);
+  b += (jacobi ? 6 : 5) * align_up(8 * n);
   b += align_up(sizeof(double) * 4 * nblocks);
   return b;
 }
@@ -164,6 +164,7 @@ struct Job {
 struct cg_batch_ctx {
   int device = 0;
   bool mixed = false;
+  bool jacobi = false;
   int max_systems = 1024;
   int chunk_iters = 0;
   int replace_every = 50;
@@ -183,6 +184,8 @@ struct cg_batch_ctx {
   cgk::SolveCtrl* d_ctrl = nullptr;
   cgk::BatchQueue* d_queue = nullptr;
   int32_t* d_next = nullptr;
+  int32_t* d_admit_err = nullptr;      // Jacobi: first row without a positive diagonal (+1)
+  int32_t* h_admit_err = nullptr;      // pinned
   cgk::SolveParams* h_sys = nullptr;   // pinned
   cgk::SolveCtrl* h_ctrl = nullptr;    // pinned
   cgk::BatchQueue* h_queue = nullptr;  // pinned
@@ -229,7 +232,7 @@ cudaError_t enqueue_round(cg_batch_ctx* b) {
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(int32_t), b->compute);
   if (e == cudaSuccess) {
     cgk::BatchParams P{b->d_sys, b->d_queue, b->d_next};
-    e = cgk::launch_batch(P, b->mixed, b->nblocks, b->compute);
+    e = cgk::launch_batch(P, b->mixed, b->jacobi, b->nblocks, b->compute);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(cgk::SolveCtrl) * b->max_systems, cudaMemcpyDeviceToHost,
@@ -299,10 +302,10 @@ bool load_structure(const cg_request& r, bool validate, std::vector<int32_t>& rp
 
 // A job's device layout inside its arena block.
 struct Layout {
-  size_t rp, col, val, val32, step, mode, bstep, brow, b, x, r, p, q, p32, part, total;
+  size_t rp, col, val, val32, step, mode, bstep, brow, b, x, r, p, q, p32, dinv, part, total;
 };
 
-Layout layout_of(int64_t n, int64_t nnz, size_t nsteps2, int group, bool mixed) {
+Layout layout_of(int64_t n, int64_t nnz, size_t nsteps2, int group, bool mixed, bool jacobi) {
   const size_t pad = cgk::kPadEntries;
   Layout L{};
   size_t o = 0;
@@ -325,6 +328,7 @@ Layout layout_of(int64_t n, int64_t nnz, size_t nsteps2, int group, bool mixed) 
   L.p = take(8 * n);
   L.q = take(8 * n);
   L.p32 = mixed ? take(4 * n) : 0;
+  L.dinv = jacobi ? take(8 * n) : 0;
   L.part = take(sizeof(double) * 4 * group);
   L.total = o;
   return L;
@@ -366,7 +370,7 @@ void admit(cg_batch_ctx* b) {
                                             : auto_group(b->model, n, nnz, b->mixed, b->nblocks);
     cgh::Partition part;
     cgh::build_partition(rp, n, group, part);
-    const Layout L = layout_of(n, nnz, part.step.size(), group, b->mixed);
+    const Layout L = layout_of(n, nnz, part.step.size(), group, b->mixed, b->jacobi);
     size_t off = 0;
     int slot = -1;
     {
@@ -420,6 +424,13 @@ void admit(cg_batch_ctx* b) {
     step(cudaMemcpyAsync(at(L.b), r.b, 8 * n, is_device_ptr(r.b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          s));
     step(cudaMemsetAsync(at(L.x), 0, 8 * n, s));
+    if (b->jacobi) {
+      step(cudaMemsetAsync(b->d_admit_err, 0, sizeof(int32_t), s));
+      step(cgk::launch_jacobi_dinv(reinterpret_cast<int32_t*>(at(L.rp)), reinterpret_cast<int32_t*>(at(L.col)),
+                                   reinterpret_cast<double*>(at(L.val)), n, reinterpret_cast<double*>(at(L.dinv)),
+                                   b->d_admit_err, s));
+      step(cudaMemcpyAsync(b->h_admit_err, b->d_admit_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     step(cudaMemsetAsync(b->d_ctrl + slot, 0, sizeof(cgk::SolveCtrl), s));
     cgk::SolveParams& P = b->h_sys[slot];
     std::memset(&P, 0, sizeof(P));
@@ -449,10 +460,22 @@ void admit(cg_batch_ctx* b) {
     P.wait_limit_ns = b->wait_ns;
     P.group = group;
     P.chunk_iters = b->chunk_iters;
+    P.dinv = b->jacobi ? reinterpret_cast<double*>(at(L.dinv)) : nullptr;
     step(cudaMemcpyAsync(b->d_sys + slot, &P, sizeof(P), cudaMemcpyHostToDevice, s));
     // the host vectors must outlive the copies
     step(cudaStreamSynchronize(s));
     j->d_x = reinterpret_cast<double*>(at(L.x));
+    if (e == cudaSuccess && b->jacobi && *b->h_admit_err != 0) {
+      std::lock_guard<std::mutex> lk(b->mu);
+      b->arena.release(j->off, j->bytes);
+      b->free_slots.push_back(slot);
+      j->slot = -1;
+      finish_without_device(b, j, CG_EINVAL);
+      b->err = "request " + std::to_string(j->ticket) + ": Jacobi preconditioner: diagonal of row " +
+               std::to_string(*b->h_admit_err - 1) + " is not positive";
+      b->cv_done.notify_all();
+      continue;
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       std::lock_guard<std::mutex> lk(b->mu);
@@ -632,6 +655,8 @@ void release_all(cg_batch_ctx* b) {
   if (b->d_ctrl) cudaFree(b->d_ctrl);
   if (b->d_queue) cudaFree(b->d_queue);
   if (b->d_next) cudaFree(b->d_next);
+  if (b->d_admit_err) cudaFree(b->d_admit_err);
+  if (b->h_admit_err) cudaFreeHost(b->h_admit_err);
   if (b->h_sys) cudaFreeHost(b->h_sys);
   if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
   if (b->h_queue) cudaFreeHost(b->h_queue);
@@ -670,6 +695,7 @@ void cg_batch_opts_default(cg_batch_opts* o) {
   o->use_graph = 1;
   o->group_override = 0;
   o->validate = 1;
+  o->preconditioner = CG_PRECOND_NONE;
 }
 
 const char* cg_batch_last_error(cg_batch b) {
@@ -689,7 +715,8 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   if (o.precision != CG_PREC_FP64 && o.precision != CG_PREC_MIXED)
     return bfail(nullptr, CG_EINVAL, "cg_batch_create: unknown precision");
   if (o.max_systems <= 0 || o.max_systems > (1 << 20) || o.chunk_iters < 0 || o.replace_every < 0 ||
-      o.budget_bytes < 0 || o.max_pending <= 0 || o.group_override < 0)
+      o.budget_bytes < 0 || o.max_pending <= 0 || o.group_override < 0 ||
+      (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI))
     return bfail(nullptr, CG_EINVAL, "cg_batch_create: bad option");
   auto b = std::make_unique<cg_batch_ctx>();
   if (o.device >= 0) b->device = o.device;
@@ -699,6 +726,7 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
     return bfail(nullptr, CG_ECUDA, "cg_batch_create: cannot use the device");
   }
   b->mixed = o.precision == CG_PREC_MIXED;
+  b->jacobi = o.preconditioner == CG_PRECOND_JACOBI;
   b->max_systems = o.max_systems;
   b->chunk_iters = o.chunk_iters;
   b->replace_every = o.replace_every;
@@ -711,7 +739,7 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
 
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int per_sm = e == cudaSuccess ? cgk::batch_blocks_per_sm(b->mixed) : -1;
+  const int per_sm = e == cudaSuccess ? cgk::batch_blocks_per_sm(b->mixed, b->jacobi) : -1;
   if (e != cudaSuccess || per_sm <= 0) {
     cudaGetLastError();
     return bfail(nullptr, CG_ECUDA, "cg_batch_create: the batch kernel cannot be resident");
@@ -750,11 +778,12 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   if ((e = cudaMalloc(&b->d_sys, sizeof(cgk::SolveParams) * b->max_systems)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_ctrl, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_queue, b->queue_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_next, 16)) != cudaSuccess)
+      (e = cudaMalloc(&b->d_next, 16)) != cudaSuccess || (e = cudaMalloc(&b->d_admit_err, 16)) != cudaSuccess)
     return fail_cuda(e, "cg_batch_create: tables");
   if ((e = cudaMallocHost(&b->h_sys, sizeof(cgk::SolveParams) * b->max_systems)) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_ctrl, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||
-      (e = cudaMallocHost(&b->h_queue, b->queue_bytes)) != cudaSuccess)
+      (e = cudaMallocHost(&b->h_queue, b->queue_bytes)) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_admit_err, 16)) != cudaSuccess)
     return fail_cuda(e, "cg_batch_create: pinned tables");
   std::memset(b->h_queue, 0, b->queue_bytes);
   if ((e = cudaMemset(b->d_ctrl, 0, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||
@@ -796,7 +825,7 @@ int cg_batch_submit(cg_batch b, const cg_request* reqs, int32_t count, uint64_t*
     std::string why;
     if (!request_ok(reqs[i], why))
       return bfail(b, CG_EINVAL, "cg_batch_submit: request " + std::to_string(i) + ": " + why);
-    const size_t need = footprint_bound(reqs[i].n, reqs[i].nnz, b->mixed, b->nblocks);
+    const size_t need = footprint_bound(reqs[i].n, reqs[i].nnz, b->mixed, b->jacobi, b->nblocks);
     if (need > b->arena.cap())
       return bfail(b, CG_ENOMEM, "cg_batch_submit: request " + std::to_string(i) + " needs up to " +
                                      std::to_string(need) + " bytes, more than the budget of " +

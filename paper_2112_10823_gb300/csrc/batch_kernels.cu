@@ -15,7 +15,7 @@ namespace cgk {
 // group start together; the rest are one-CTA tasks, taken in queue order as
 // CTAs free up.  Between tasks the whole CTA (producer included) joins, the
 // producer having drained its copies, and the ring barriers are reset.
-template <bool kMixed>
+template <bool kMixed, bool kJacobi>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __gr
     stream_setup(sm, cs, P.A, tk.rank, reinit);
     reinit = true;
     if (threadIdx.x >= kConsumers) solve_producer<kMixed>(sm, cs, P);
-    else solve_consumers<kMixed>(sm, cs, P, tk.rank);
+    else solve_consumers<kMixed, kJacobi>(sm, cs, P, tk.rank);
     __syncthreads();  // producer drained, consumers done: the CTA is free
   }
 }
@@ -52,10 +52,16 @@ cudaError_t batch_smem_attr(const void* kernel, size_t bytes) {
 }
 }  // namespace
 
-int batch_blocks_per_sm(bool mixed) {
+const void* batch_kernel_ptr(bool mixed, bool jacobi) {
+  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_batch_kernel<true, true>)
+                           : reinterpret_cast<const void*>(cg_batch_kernel<true, false>);
+  return jacobi ? reinterpret_cast<const void*>(cg_batch_kernel<false, true>)
+                : reinterpret_cast<const void*>(cg_batch_kernel<false, false>);
+}
+
+int batch_blocks_per_sm(bool mixed, bool jacobi) {
   int nb = 0;
-  const void* k = mixed ? reinterpret_cast<const void*>(cg_batch_kernel<true>)
-                        : reinterpret_cast<const void*>(cg_batch_kernel<false>);
+  const void* k = batch_kernel_ptr(mixed, jacobi);
   cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, RingSmem::kBytes);
   return e == cudaSuccess ? nb : -1;
@@ -64,9 +70,8 @@ int batch_blocks_per_sm(bool mixed) {
 // Cooperative launch (all CTAs co-resident: the ranks of a group wait on
 // each other), through cudaLaunchKernelEx so that it can be captured in a
 // CUDA graph.
-cudaError_t launch_batch(const BatchParams& B, bool mixed, int nblocks, cudaStream_t s) {
-  const void* k = mixed ? reinterpret_cast<const void*>(cg_batch_kernel<true>)
-                        : reinterpret_cast<const void*>(cg_batch_kernel<false>);
+cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblocks, cudaStream_t s) {
+  const void* k = batch_kernel_ptr(mixed, jacobi);
   cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -100,6 +100,7 @@ struct cg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int precision = CG_PREC_FP64;
+  int preconditioner = CG_PRECOND_NONE;
   int replace_every = 50;
   unsigned long long wait_limit_ns = 2000000000ull;
   int64_t n = 0, nnz = 0;
@@ -119,6 +120,7 @@ struct cg_ctx {
   double* d_p = nullptr;
   double* d_q = nullptr;
   float* d_p32 = nullptr;
+  double* d_dinv = nullptr;   // Jacobi: 1 / diag(A)
   double* d_xbuf = nullptr;   // staging of host x
   double* d_bbuf = nullptr;   // staging of host b
   double* d_partials = nullptr;
@@ -220,6 +222,7 @@ void cg_opts_default(cg_opts* o) {
   o->replace_every = 50;
   o->validate = 1;
   o->wait_limit_ms = 2000;
+  o->preconditioner = CG_PRECOND_NONE;
 }
 
 const char* cg_last_error(cg_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
@@ -239,6 +242,8 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   if (o.precision != CG_PREC_FP64 && o.precision != CG_PREC_MIXED)
     return fail(nullptr, CG_EINVAL, "cg_create: unknown precision");
   if (o.replace_every < 0) return fail(nullptr, CG_EINVAL, "cg_create: replace_every must be >= 0");
+  if (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI)
+    return fail(nullptr, CG_EINVAL, "cg_create: unknown preconditioner");
   if (!csr->row_ptr || (nnz > 0 && (!csr->col_idx || !csr->val)))
     return fail(nullptr, CG_EINVAL, "cg_create: NULL CSR array");
 
@@ -274,6 +279,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   DeviceGuard guard(h->device);
   h->stream = static_cast<cudaStream_t>(o.stream);
   h->precision = o.precision;
+  h->preconditioner = o.preconditioner;
   h->replace_every = o.replace_every;
   h->wait_limit_ns = static_cast<unsigned long long>(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
   h->n = n;
@@ -315,7 +321,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   int sms = 0;
   CG_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "cg_create: SM count");
   h->num_sms = sms;
-  const int per_sm = cgk::solve_blocks_per_sm(o.precision == CG_PREC_MIXED);
+  const int per_sm = cgk::solve_blocks_per_sm(o.precision == CG_PREC_MIXED, o.preconditioner == CG_PRECOND_JACOBI);
   if (per_sm <= 0) {
     int rc = fail(nullptr, CG_ECUDA, "cg_create: the solve kernel cannot be resident (occupancy 0)");
     release(h);
@@ -356,6 +362,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     CG_TRY(dalloc(h, &h->d_val32, nnz + pad), "cg_create: cudaMalloc");
     CG_TRY(dalloc(h, &h->d_p32, n), "cg_create: cudaMalloc");
   }
+  if (o.preconditioner == CG_PRECOND_JACOBI) CG_TRY(dalloc(h, &h->d_dinv, n), "cg_create: cudaMalloc");
   CG_TRY(cudaMallocHost(&h->h_ctrl, sizeof(cgk::SolveCtrl)), "cg_create: cudaMallocHost");
 
   CG_TRY(cudaMemcpy(h->d_row_ptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice), "cg_create: upload");
@@ -387,6 +394,19 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   if (o.precision == CG_PREC_MIXED) {
     CG_TRY(cudaMemset(h->d_val32, 0, sizeof(float) * (nnz + pad)), "cg_create: memset");
     if (nnz > 0) CG_TRY(cgk::launch_f64_to_f32(nnz, h->d_val, h->d_val32, nullptr), "cg_create: FP32 copy");
+  }
+  if (o.preconditioner == CG_PRECOND_JACOBI) {
+    CG_TRY(cgk::launch_jacobi_dinv(h->d_row_ptr, h->d_col, h->d_val, n, h->d_dinv, h->d_err, nullptr),
+           "cg_create: Jacobi diagonal");
+    int32_t bad_row = 0;
+    CG_TRY(cudaMemcpy(&bad_row, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost), "cg_create: read-back");
+    if (bad_row != 0) {
+      release(h);
+      delete h;
+      return fail(nullptr, CG_EINVAL, "cg_create: Jacobi preconditioner: diagonal of row " +
+                                          std::to_string(bad_row - 1) + " is not positive (A is not SPD)");
+    }
+    CG_TRY(cudaMemset(h->d_err, 0, 16), "cg_create: memset");
   }
   CG_TRY(cudaDeviceSynchronize(), "cg_create: synchronize");
 #undef CG_TRY
@@ -489,6 +509,7 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   P.group = h->nblocks;
   P.pad = 0;
   P.chunk_iters = 0;
+  P.dinv = h->d_dinv;
   e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: cooperative launch");
   e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(cgk::SolveCtrl), cudaMemcpyDeviceToHost, h->stream);

@@ -75,9 +75,9 @@ struct SolveCtrl {
   int32_t abort;                // set by any CTA that gives up (timeout)
   int32_t status;               // CG_* code
   int64_t iters;                // steps done
-  double rho;                   // r.r of the current iterate (recursive residual)
+  double rho;                   // r.z of the current iterate (r.r without preconditioner)
   double bnorm2;                // b.b
-  double relres_rec;            // sqrt(rho)/||b||
+  double relres_rec;            // ||r||/||b|| of the recursive residual
   double relres_true;           // ||b - A x|| / ||b||
   int32_t timeout_site;         // which wait gave up (diagnostics)
   int32_t phase;                // SolvePhase
@@ -103,6 +103,7 @@ struct SolveParams {
   int32_t group;                // CTAs that solve this system together (its partition's CTA count)
   int32_t pad;
   int64_t chunk_iters;          // steps per launch (<= 0: until the solve ends)
+  const double* dinv;           // Jacobi preconditioner 1/diag(A), or nullptr (plain CG)
 };
 
 // Batched solves: one persistent launch over many systems.  Every CTA takes
@@ -129,16 +130,20 @@ enum : int32_t {
 };
 
 // Launchers (defined in the .cu files; return the CUDA error of the launch).
+// dinv[i] = 1 / (sum of row i's stored entries in column i); err set to the
+// first row (+1) whose diagonal is not positive.
+cudaError_t launch_jacobi_dinv(const int32_t* row_ptr, const int32_t* col_idx, const double* val, int64_t n,
+                               double* dinv, int32_t* err, cudaStream_t s);
 cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* err, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out,
                        double* partials, unsigned int* counter, int grid, cudaStream_t s);
 cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_ewmul(int64_t n, const double* x, const double* y, double* z, cudaStream_t s);
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s);
-int solve_blocks_per_sm(bool mixed);   // occupancy of the persistent kernel
+int solve_blocks_per_sm(bool mixed, bool jacobi);   // occupancy of the persistent kernel
 // The batched solve (cooperative launch of `nblocks` CTAs, one per SM).
-cudaError_t launch_batch(const BatchParams& B, bool mixed, int nblocks, cudaStream_t s);
-int batch_blocks_per_sm(bool mixed);
+cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblocks, cudaStream_t s);
+int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
 // Shared-memory bytes of the streamed product (ring + scratch).

@@ -29,8 +29,9 @@
 
 namespace cgk {
 
-// One system on the whole grid: CTA c is rank c of the group.
-template <bool kMixed>
+// One system on the whole grid: CTA c is rank c of the group.  kJacobi:
+// preconditioned by M = diag(A) (P.dinv).
+template <bool kMixed, bool kJacobi>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     solve_producer<kMixed>(sm, cs, P);
     return;
   }
-  solve_consumers<kMixed>(sm, cs, P, blockIdx.x);
+  solve_consumers<kMixed, kJacobi>(sm, cs, P, blockIdx.x);
 }
 
 // y = A x (same partition and stream as the solve; one pass).
@@ -87,33 +88,55 @@ cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* er
 
 size_t spmv_smem_bytes() { return RingSmem::kBytes; }
 
-int solve_blocks_per_sm(bool mixed) {
+const void* solve_kernel_ptr(bool mixed, bool jacobi) {
+  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<true, true>)
+                           : reinterpret_cast<const void*>(cg_solve_kernel<true, false>);
+  return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<false, true>)
+                : reinterpret_cast<const void*>(cg_solve_kernel<false, false>);
+}
+
+int solve_blocks_per_sm(bool mixed, bool jacobi) {
   int nb = 0;
-  cudaError_t e;
-  if (mixed) {
-    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), RingSmem::kBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<true>, kBlock, RingSmem::kBytes);
-  } else {
-    e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), RingSmem::kBytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_solve_kernel<false>, kBlock, RingSmem::kBytes);
-  }
+  const void* k = solve_kernel_ptr(mixed, jacobi);
+  cudaError_t e = ensure_smem_attr(k, RingSmem::kBytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, RingSmem::kBytes);
   return e == cudaSuccess ? nb : -1;
 }
 
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
   void* args[] = {const_cast<SolveParams*>(&P)};
-  if (mixed) {
-    cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<true>), RingSmem::kBytes);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_solve_kernel<true>), dim3(P.A.nblocks),
-                                       dim3(kBlock), args, RingSmem::kBytes, s);
-  }
-  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cg_solve_kernel<false>), RingSmem::kBytes);
+  const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr);
+  cudaError_t e = ensure_smem_attr(k, RingSmem::kBytes);
   if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_solve_kernel<false>), dim3(P.A.nblocks),
-                                     dim3(kBlock), args, RingSmem::kBytes, s);
+  return cudaLaunchCooperativeKernel(k, dim3(P.A.nblocks), dim3(kBlock), args, RingSmem::kBytes, s);
+}
+
+// dinv[i] = 1 / diag(A)_i (the diagonal summed over row i's entries in
+// column i, in storage order); err <- first row (+1) without a positive one.
+__global__ void jacobi_dinv_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                   const double* __restrict__ val, int64_t n, double* __restrict__ dinv,
+                                   int32_t* err) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double d = 0.0;
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+      if (col_idx[k] == i) d += val[k];
+    if (d > 0.0) {
+      dinv[i] = 1.0 / d;
+    } else {
+      dinv[i] = 0.0;
+      atomicCAS(err, 0, static_cast<int32_t>(i + 1));
+    }
+  }
+}
+
+cudaError_t launch_jacobi_dinv(const int32_t* row_ptr, const int32_t* col_idx, const double* val, int64_t n,
+                               double* dinv, int32_t* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  jacobi_dinv_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(row_ptr, col_idx, val, n,
+                                                                                        dinv, err);
+  return cudaGetLastError();
 }
 
 // ---- self-test of the bounded wait: one CTA (of kConsumers threads, the

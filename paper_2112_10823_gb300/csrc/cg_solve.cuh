@@ -48,7 +48,7 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
 // launch saved, for at most P.chunk_iters steps.
-template <bool kMixed>
+template <bool kMixed, bool kJacobi>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
                                                 const int rank) {
   const DevCsr& A = P.A;
@@ -65,6 +65,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   double* __restrict__ p = P.p;
   double* __restrict__ q = P.q;
   float* __restrict__ p32 = P.p32;
+  const double* __restrict__ dinv = P.dinv;  // Jacobi (kJacobi): z = dinv .* r; plain CG: z = r
   const int nb = P.group;
   ConsumerCursor cur;
   GridBarrier gb;
@@ -79,30 +80,64 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     slot = __ldcg(&ctrl->slot);
   }
 
-  // Grid-wide sum of one value per thread, identical in every CTA.  Each CTA
-  // sums its threads in fixed point, publishes the result, and after a grid
-  // barrier every CTA sums the nb CTA values, again in fixed point (exact and
-  // order-independent, hence the same bits everywhere).  Two slots of
-  // partials alternate so that a fast CTA publishing the next sum never
-  // overwrites values a slow CTA is still reading.
-  auto allreduce = [&](double v, double& out) -> bool {
-    const double cta = fx_block_sum(v, fx);
-    if (nb == 1) {  // a one-CTA group: the CTA sum is the sum
-      out = cta;
-      return true;
-    }
-    double* part = P.partials + static_cast<size_t>(slot) * nb;
-    if (tid == 0) part[rank] = cta;
-    if (!gb.sync(ctrl, lim, ++site, flag)) return false;
+  // Group-wide sums of one or two values per thread, identical in every CTA.
+  // Each CTA sums its threads in fixed point, publishes the result, and after
+  // a group barrier every CTA sums the nb CTA values, again in fixed point
+  // (exact and order-independent, hence the same bits everywhere).  Two
+  // slots of partials (2 nb values each) alternate so that a fast CTA
+  // publishing the next sum never overwrites values a slow CTA is still
+  // reading.
+  auto group_sum = [&](const double* part) -> double {
     double mine[kMaxCtaSums];
 #pragma unroll
     for (int j = 0; j < kMaxCtaSums; ++j) {
       const int c = tid + j * kConsumers;
       mine[j] = c < nb ? __ldcg(part + c) : 0.0;
     }
-    out = fx_block_sum<kMaxCtaSums>(mine, fx);
+    return fx_block_sum<kMaxCtaSums>(mine, fx);
+  };
+  auto allreduce = [&](double v, double& out) -> bool {
+    const double cta = fx_block_sum(v, fx);
+    if (nb == 1) {  // a one-CTA group: the CTA sum is the sum
+      out = cta;
+      return true;
+    }
+    double* part = P.partials + static_cast<size_t>(slot) * 2 * nb;
+    if (tid == 0) part[rank] = cta;
+    if (!gb.sync(ctrl, lim, ++site, flag)) return false;
+    out = group_sum(part);
     slot ^= 1;
     return true;
+  };
+  auto allreduce2 = [&](double v1, double v2, double& o1, double& o2) -> bool {
+    const double c1 = fx_block_sum(v1, fx);
+    const double c2 = fx_block_sum(v2, fx);
+    if (nb == 1) {
+      o1 = c1;
+      o2 = c2;
+      return true;
+    }
+    double* part = P.partials + static_cast<size_t>(slot) * 2 * nb;
+    if (tid == 0) {
+      part[rank] = c1;
+      part[nb + rank] = c2;
+    }
+    if (!gb.sync(ctrl, lim, ++site, flag)) return false;
+    o1 = group_sum(part);
+    o2 = group_sum(part + nb);
+    slot ^= 1;
+    return true;
+  };
+  // r.r and (Jacobi) r.z of per-thread partials: one sum without a
+  // preconditioner (r.z = r.r), both in one group barrier with one
+  auto sums_rr_rz = [&](double acc_rr, double acc_rz, double& rr, double& rz) -> bool {
+    if constexpr (kJacobi) {
+      return allreduce2(acc_rr, acc_rz, rr, rz);
+    } else {
+      if (!allreduce(acc_rr, rr)) return false;
+      rz = rr;
+      return true;
+    }
   };
   // The products outside the step loop (setup, true residual at the end,
   // and the mixed solve's residual replacements) read the FP64 values and
@@ -118,25 +153,32 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     return cta_and(ok);
   };
 
-  double rho, bnorm2;
+  // rho = r.z (the preconditioned inner product; r.r without a
+  // preconditioner), rr = r.r (the stopping test always uses ||r||)
+  double rho, bnorm2, rr;
   int64_t k = 0;
   if (phase0 == kPhaseRunning) {
     rho = __ldcg(&ctrl->rho);
     bnorm2 = __ldcg(&ctrl->bnorm2);
     k = __ldcg(&ctrl->iters);
+    rr = __ldcg(&ctrl->relres_rec);
+    rr = rr * rr * bnorm2;
   } else {
-    // ---- setup: r = b - A x, p = r, rho = r.r, ||b||^2
-    double acc_rr = 0.0, acc_bb = 0.0;
+    // ---- setup: r = b - A x, z = dinv .* r, p = z, rho = r.z, ||b||^2
+    double acc_rr = 0.0, acc_bb = 0.0, acc_rz = 0.0;
     auto epi = [&](int i, double s, double bi) {
       const double ri = bi - s;
+      double zi = ri;
+      if constexpr (kJacobi) zi = dinv[i] * ri;
       r[i] = ri;
-      p[i] = ri;
-      if constexpr (kMixed) p32[i] = static_cast<float>(ri);
+      p[i] = zi;
+      if constexpr (kMixed) p32[i] = static_cast<float>(zi);
       acc_rr = fma(ri, ri, acc_rr);
+      if constexpr (kJacobi) acc_rz = fma(ri, zi, acc_rz);
       acc_bb = fma(bi, bi, acc_bb);
     };
     if (!product64(x, b, epi)) { solve_fail(sm, P); return; }
-    if (!allreduce(acc_rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, P); return; }
+    if (!sums_rr_rz(acc_rr, acc_rz, rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, P); return; }
   }
   if (bnorm2 == 0.0) {  // b = 0: the solution is 0
     for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = 0.0;
@@ -157,7 +199,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   const double thresh2 = (P.tol * P.tol) * bnorm2;
   const int64_t k_end = P.chunk_iters > 0 && P.chunk_iters < P.maxit - k ? k + P.chunk_iters : P.maxit;
   int32_t status = kOK;
-  bool done = rho <= thresh2;
+  bool done = phase0 != kPhaseRunning && rr <= thresh2;
 
   while (!done && k < P.maxit) {
     // ---- q = A p, gamma = p.q
@@ -188,65 +230,77 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     cta_sync();
     const double alpha = sc[0];
 
-    // ---- r -= alpha q, rho' = r.r   (four rows per thread in flight)
-    double acc_r = 0.0;
-    for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-      double qv[4], rv[4];
+    // ---- r -= alpha q, rr' = r.r, rho' = r.z   (four rows per thread in flight)
+    double acc_r = 0.0, acc_z = 0.0;
+    {
+      constexpr bool jac = kJacobi;
+      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
+        double qv[4], rv[4], dv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = base + u * kConsumers;
-        if (i < row1) { qv[u] = q[i]; rv[u] = r[i]; }
-      }
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kConsumers;
+          if (i < row1) {
+            qv[u] = q[i];
+            rv[u] = r[i];
+            if constexpr (jac) dv[u] = dinv[i];
+          }
+        }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = base + u * kConsumers;
-        if (i < row1) {
-          const double rn = fma(-alpha, qv[u], rv[u]);
-          r[i] = rn;
-          acc_r = fma(rn, rn, acc_r);
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kConsumers;
+          if (i < row1) {
+            const double rn = fma(-alpha, qv[u], rv[u]);
+            r[i] = rn;
+            acc_r = fma(rn, rn, acc_r);
+            if constexpr (jac) acc_z = fma(rn, dv[u] * rn, acc_z);
+          }
         }
       }
     }
     double rho_new;
-    if (!allreduce(acc_r, rho_new)) { solve_fail(sm, P); return; }
+    if (!sums_rr_rz(acc_r, acc_z, rr, rho_new)) { solve_fail(sm, P); return; }
     ++k;
 
     bool replace = false;
-    if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rho_new <= thresh2;
+    if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rr <= thresh2;
     if (replace) {
       // x += alpha p, then r = b - A x in FP64 (residual replacement).  The
       // direction keeps the recurrence's beta = rho_rec / rho (rho_rec: the
-      // recursive r.r of this step); r and rho take the true residual's values.
+      // recursive r.z of this step); r, rr and rho take the true residual's
+      // values.
       if (tid == 0) sc[1] = rho_new / rho;
       for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
       if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
       const double beta = sc[1];
-      double acc_t = 0.0;
+      double acc_t = 0.0, acc_tz = 0.0;
       auto epi = [&](int i, double s, double bi) {
         const double ri = bi - s;
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
+        if constexpr (kJacobi) acc_tz = fma(ri, dinv[i] * ri, acc_tz);
       };
-      if (!product64(x, b, epi) || !allreduce(acc_t, rho_new)) { solve_fail(sm, P); return; }
-      if (rho_new <= thresh2) {
+      if (!product64(x, b, epi) || !sums_rr_rz(acc_t, acc_tz, rr, rho_new)) { solve_fail(sm, P); return; }
+      if (rr <= thresh2) {
         rho = rho_new;
         done = true;
         break;
       }
       for (int i = row0 + tid; i < row1; i += kConsumers) {
-        const double pi = fma(beta, p[i], r[i]);
+        double zi = r[i];
+        if constexpr (kJacobi) zi = dinv[i] * zi;
+        const double pi = fma(beta, p[i], zi);
         p[i] = pi;
         if constexpr (kMixed) p32[i] = static_cast<float>(pi);
       }
       rho = rho_new;
     } else {
-      if (!kMixed && rho_new <= thresh2) {
+      if (!kMixed && rr <= thresh2) {
         for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
         rho = rho_new;
         done = true;
         break;
       }
-      // ---- x += alpha p; p = r + beta p
+      // ---- x += alpha p; p = z + beta p   (z = dinv .* r, or r)
       if (tid == 0) sc[1] = rho_new / rho;
       cta_sync();
       const double beta = sc[1];
@@ -255,7 +309,12 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = base + u * kConsumers;
-          if (i < row1) { pv[u] = p[i]; rv[u] = r[i]; xv[u] = x[i]; }
+          if (i < row1) {
+            pv[u] = p[i];
+            rv[u] = r[i];
+            if constexpr (kJacobi) rv[u] = dinv[i] * rv[u];
+            xv[u] = x[i];
+          }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -278,7 +337,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         ctrl->iters = k;
         ctrl->rho = rho;
         ctrl->bnorm2 = bnorm2;
-        ctrl->relres_rec = sqrt(rho / bnorm2);
+        ctrl->relres_rec = sqrt(rr / bnorm2);
         ctrl->rounds = gb.target / gb.count;
         ctrl->slot = slot;
         ctrl->phase = kPhaseRunning;
@@ -306,7 +365,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     ctrl->iters = k;
     ctrl->rho = rho;
     ctrl->bnorm2 = bnorm2;
-    ctrl->relres_rec = sqrt(rho / bnorm2);
+    ctrl->relres_rec = sqrt(rr / bnorm2);
     ctrl->relres_true = sqrt(acc_t / bnorm2);
     ctrl->phase = kPhaseDone;
   }

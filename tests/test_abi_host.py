@@ -86,6 +86,12 @@ def test_bad_arguments_rejected(built):
     with pytest.raises(cg.CGError) as e:
         cg.cg_create(A.row_ptr, A.col_idx, A.val, precision=7)
     assert e.value.status == cg.CG_EINVAL
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.row_ptr, A.col_idx, A.val, preconditioner=7)
+    assert e.value.status == cg.CG_EINVAL
+    with pytest.raises(cg.CGError) as e:
+        cg.Batch(precision=7)
+    assert e.value.status == cg.CG_EINVAL
     # one-based input validated as one-based
     B = fi.to_one_based(A)
     with pytest.raises(cg.CGError):
@@ -101,4 +107,15 @@ def test_no_gpu_fails_loudly(built):
     A = fi.laplace7(3)
     with pytest.raises(cg.CGError) as e:
         cg.cg_create(A.row_ptr, A.col_idx, A.val)
+    assert e.value.status in (cg.CG_ECUDA, cg.CG_ENOMEM)
+
+
+def test_batch_without_gpu_fails_loudly(built):
+    """The batched interface has no CPU path either."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2112_10823_gb300 as cg
+    with pytest.raises(cg.CGError) as e:
+        cg.Batch()
     assert e.value.status in (cg.CG_ECUDA, cg.CG_ENOMEM)
