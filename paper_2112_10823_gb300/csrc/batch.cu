@@ -106,7 +106,7 @@ double bytes_per_step(int64_t n, int64_t nnz, bool mixed) {
 
 int auto_group(const GroupModel& m, int64_t n, int64_t nnz, bool mixed, int nblocks) {
   const int gmax = std::max<int64_t>(1, std::min<int64_t>({static_cast<int64_t>(nblocks / 2),
-                                                           static_cast<int64_t>(2 * cgk::kConsumers),
+                                                           static_cast<int64_t>(1024),
                                                            n / 4096}));
   const double steps = est_steps(m, n), bs = bytes_per_step(n, nnz, mixed);
   for (int g = 1; g <= gmax; ++g) {
@@ -140,7 +140,7 @@ size_t footprint_bound(int64_t n, int64_t nnz, bool mixed, bool jacobi, int nblo
   b += align_up(sizeof(int4) * (n + 2)) + align_up(4 * (n + 2));
   b += 2 * align_up(4 * (static_cast<size_t>(nblocks) + 1));
   b += (jacobi ? 6 : 5) * align_up(8 * n);
-  b += align_up(sizeof(double) * 4 * nblocks);
+  b += align_up(sizeof(double) * 6 * nblocks);
   return b;
 }
 
@@ -329,7 +329,7 @@ Layout layout_of(int64_t n, int64_t nnz, size_t nsteps2, int group, bool mixed, 
   L.q = take(8 * n);
   L.p32 = mixed ? take(4 * n) : 0;
   L.dinv = jacobi ? take(8 * n) : 0;
-  L.part = take(sizeof(double) * 4 * group);
+  L.part = take(sizeof(double) * 6 * group);
   L.total = o;
   return L;
 }

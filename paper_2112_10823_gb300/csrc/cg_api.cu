@@ -329,7 +329,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     return rc;
   }
   h->nblocks = sms * per_sm;
-  if (h->nblocks > 2 * cgk::kConsumers) {  // the grid-wide sum reads at most 2 CTA sums per thread
+  if (h->nblocks > 1024) {  // the group-wide fixed-point sum takes at most 1024 CTA values
     int rc = fail(nullptr, CG_ECUDA, "cg_create: more persistent CTAs than the grid-wide sum supports");
     release(h);
     delete h;
@@ -353,7 +353,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(dalloc(h, &h->d_q, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_xbuf, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_bbuf, n), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_partials, static_cast<size_t>(4) * h->nblocks), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_partials, static_cast<size_t>(6) * h->nblocks), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_ctrl, 1), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_partials, static_cast<size_t>(4) * sms + 8), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_counter, 4), "cg_create: cudaMalloc");

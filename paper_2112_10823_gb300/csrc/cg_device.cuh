@@ -134,88 +134,173 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[nt];
 }
 
-// Scratch of the fixed-point CTA sum (shared memory).
-struct FxScratch {
-  long long m[kWarps];
-  int32_t e[kWarps];
-  int32_t nf[kWarps];
-  double result;
+// -------------------------------------------- warp-level fixed-point sums
+
+// A partial of an exact fixed-point sum: the integer m at scale 2^(e - 1074),
+// e being the largest biased exponent among the values summed; nf: a NaN or
+// an infinity was among them.
+struct FxPart {
+  long long m;
+  int32_t e;
+  int32_t nf;
 };
 
-// Sum over the CTA of K doubles per thread, exactly in fixed point.
-//
-// FP64 adds cost 64 cycles of latency each on this GPU, so a tree of them over
-// hundreds of values sits on the critical path of every CG step.  Instead each
-// value is rounded to a common fixed-point grid set by the largest exponent E
-// among all values (spacing 2^(E-1074), i.e. about 2^-51 of the largest value,
-// leaving 10 bits of headroom for up to 1024 terms), the integers are added
-// exactly with integer adds (order-independent, so the sum is deterministic
-// whatever the order of arrival), and the total is rounded once back to FP64.
-// Zero and subnormal values count as zero; an infinite or NaN value makes the
-// sum NaN.  Thread 0 converts the total; every thread receives it through
-// shared memory.  Called by the kConsumers consumer threads (K * kConsumers
-// <= 1024).
-template <int K>
-__device__ __forceinline__ double fx_block_sum(const double (&v)[K], FxScratch* sc) {
-  static_assert(K * kConsumers <= 1024, "fixed-point headroom is 10 bits");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long bits[K];
-  int e[K];
-  int emax = 0, nfl = 0;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    bits[j] = static_cast<unsigned long long>(__double_as_longlong(v[j]));
-    e[j] = static_cast<int>((bits[j] >> 52) & 0x7ffull);
-    emax = max(emax, e[j]);
-    nfl |= (e[j] == 0x7ff);
-  }
-  const unsigned int ew = __reduce_max_sync(0xffffffffu, static_cast<unsigned int>(emax));
-  const int nfw = __any_sync(0xffffffffu, nfl);
-  cta_sync();  // earlier users of sc are done
-  if (lane == 0) {
-    sc->e[warp] = static_cast<int32_t>(ew);
-    sc->nf[warp] = nfw;
-  }
-  cta_sync();
-  int E = 0, nf = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    E = max(E, static_cast<int>(sc->e[w]));
-    nf |= sc->nf[w];
-  }
+// Sum over the warp of one double per lane, exactly, in fixed point at the
+// warp's largest exponent E (spacing 2^(E-1074), about 2^-51 of the largest
+// value; 32 values leave ample headroom).  Every lane gets the same result.
+__device__ __forceinline__ FxPart fx_warp(double v) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((bits >> 52) & 0x7ffull);
+  const int E = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned int>(e)));
+  const int nf = __any_sync(0xffffffffu, e == 0x7ff);
   long long m = 0;
+  if (e != 0 && !nf) {
+    const int s = E - e + 1;  // >= 1
+    if (s < 64) {
+      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const unsigned long long rnd = (M + (1ull << (s - 1))) >> s;
+      m = (bits >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+    }
+  }
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (e[j] != 0 && !nf) {
-      const int s = E - e[j] + 1;  // >= 1
-      if (s < 64) {
-        const unsigned long long M = (bits[j] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const unsigned long long rnd = (M + (1ull << (s - 1))) >> s;
-        m += (bits[j] >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  return FxPart{m, E, nf};
+}
+
+// Sum of up to 32 partials, one per lane (`valid` lanes), realigned to the
+// largest exponent (each partial rounded once, to nearest, ties away from
+// zero) and converted to double once.  The result depends only on the
+// partials, not on their order.  Every lane gets it.
+__device__ __forceinline__ double fx_combine(FxPart p, bool valid) {
+  const int E = static_cast<int>(__reduce_max_sync(0xffffffffu, valid ? static_cast<unsigned int>(p.e) : 0u));
+  const int nf = __any_sync(0xffffffffu, valid && p.nf);
+  long long m = 0;
+  if (valid && p.m != 0) {
+    const int d = E - p.e;  // >= 0
+    if (d == 0) {
+      m = p.m;
+    } else if (d < 63) {
+      const long long a = p.m < 0 ? -p.m : p.m;
+      const long long r = (a + (1ll << (d - 1))) >> d;
+      m = p.m < 0 ? -r : r;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if (nf) return __longlong_as_double(0x7ff8000000000000ll);
+  if (E == 0) return 0.0;
+  return ldexp(static_cast<double>(m), E - 1074);
+}
+
+// Exact fixed-point sum, over the calling warp, of src[0 .. count), read
+// through L2 (values written by other CTAs); lane j takes entries j, j + 32,
+// ...; count <= 1024 keeps the integer sum within 63 bits.  The loads of a
+// batch of 8 entries per lane are all issued before any is used (one L2
+// round trip for up to 256 entries); the batch stays in registers for both
+// steps (the largest exponent, then the rounded integers).  Every lane gets
+// the result.
+__device__ __forceinline__ double fx_warp_sum_array(const double* src, int count) {
+  constexpr int kB = 8;
+  const int lane = threadIdx.x & 31;
+  long long m = 0;
+  int E = 0, nf = 0;
+  // the exponent of the whole array first (so that all batches share one grid)
+  {
+    unsigned int emax = 0;
+    int nfl = 0;
+    for (int j0 = 0; j0 < count; j0 += 32 * kB) {
+      double v[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int j = j0 + lane + 32 * u;
+        v[u] = j < count ? __ldcg(src + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v[u]));
+        const unsigned int e = static_cast<unsigned int>((bits >> 52) & 0x7ffull);
+        emax = e > emax ? e : emax;
+        nfl |= (e == 0x7ffu);
+      }
+      if (j0 + 32 * kB >= count) {
+        // last (usually only) batch: sum it from the registers
+        E = static_cast<int>(__reduce_max_sync(0xffffffffu, emax));
+        nf = __any_sync(0xffffffffu, nfl);
+        if (j0 == 0 && !nf) {
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v[u]));
+            const int e = static_cast<int>((bits >> 52) & 0x7ffull);
+            const int sh = E - e + 1;
+            if (e != 0 && sh < 64) {
+              const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+              const unsigned long long rnd = (M + (1ull << (sh - 1))) >> sh;
+              m += (bits >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (count > 32 * kB && !nf) {
+    // more than one batch: a second pass over the array at the common grid
+    for (int j0 = 0; j0 < count; j0 += 32 * kB) {
+      double v[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int j = j0 + lane + 32 * u;
+        v[u] = j < count ? __ldcg(src + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v[u]));
+        const int e = static_cast<int>((bits >> 52) & 0x7ffull);
+        const int sh = E - e + 1;
+        if (e != 0 && sh < 64) {
+          const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const unsigned long long rnd = (M + (1ull << (sh - 1))) >> sh;
+          m += (bits >> 63) ? -static_cast<long long>(rnd) : static_cast<long long>(rnd);
+        }
       }
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
-  if (lane == 0) sc->m[warp] = m;
-  cta_sync();
-  if (threadIdx.x == 0) {
-    long long tot = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) tot += sc->m[w];
-    double r;
-    if (nf) r = __longlong_as_double(0x7ff8000000000000ll);  // NaN
-    else if (E == 0) r = 0.0;
-    else r = ldexp(static_cast<double>(tot), E - 1074);
-    sc->result = r;
-  }
-  cta_sync();
-  return sc->result;
+  if (nf) return __longlong_as_double(0x7ff8000000000000ll);
+  if (E == 0) return 0.0;
+  return ldexp(static_cast<double>(m), E - 1074);
 }
 
-__device__ __forceinline__ double fx_block_sum(double v, FxScratch* sc) {
-  const double a[1] = {v};
-  return fx_block_sum<1>(a, sc);
+// Arrival and bounded wait of thread 0 at the group barrier of a system
+// (the caller synchronises its own CTA around it).  `target` is the CTA's
+// running target (in shared memory: thread 0 alone keeps it).  Returns false
+// after a wait longer than limit_ns or an abort raised by another CTA.
+__device__ __forceinline__ bool group_barrier_t0(SolveCtrl* ctrl, unsigned long long* target, unsigned int count,
+                                                 unsigned long long limit_ns, int site) {
+  *target += count;
+  if (count <= 1) return true;
+  __threadfence();
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctrl->barrier), "l"(1ull) : "memory");
+  unsigned long long t0 = 0;
+  uint32_t spins = 0;
+  const unsigned long long tgt = *target;
+  for (;;) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&ctrl->barrier) : "memory");
+    if (v >= tgt) break;
+    if ((++spins & 255u) == 0) {
+      if (*reinterpret_cast<const volatile int32_t*>(&ctrl->abort)) return false;
+      const unsigned long long now = global_timer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit_ns) {
+        atomicExch(&ctrl->abort, 1);
+        atomicExch(&ctrl->timeout_site, site);
+        return false;
+      }
+    }
+  }
+  __threadfence();
+  return true;
 }
 
 // ----------------------------------------------------------- group barrier
@@ -283,16 +368,46 @@ struct GridBarrier {
 
 // Shared memory of a solve or product CTA: the value ring (sized for FP64;
 // FP32 values use its first half) and the column-index ring, each followed by
-// its kMirror-entry mirror, the full/empty mbarriers of every slot, reduction
-// scratch and a few words (stop flag, broadcast scalars).
+// its kMirror-entry mirror, the full/empty mbarriers of every slot, the CTA
+// state of a solve, the warp partials of its sums, and a few words (stop
+// flag).
+// Per-CTA state of a solve, in shared memory: written by thread 0 (between
+// CTA barriers), read by all.  Keeping it out of registers leaves the
+// product in the step loop the registers it needs.
+struct CtaState {
+  double rho;                  // r.z (r.r without a preconditioner)
+  double rr;                   // r.r of the current iterate
+  double bnorm2;               // b.b
+  double thresh2;              // tol^2 b.b
+  double alpha, beta;
+  long long k;                 // steps done
+  long long k_end;             // last step of this launch
+  unsigned long long target;   // group-barrier target of this CTA
+  int32_t slot;                // partial-sum slot of the next group sum
+  int32_t site;                // diagnostics: group waits so far
+  int32_t ok;                  // the last group sum or barrier succeeded
+  int32_t flags;               // kFlag* below
+};
+enum : int32_t { kFlagDone = 1, kFlagBreakdown = 2, kFlagReplace = 4, kFlagResumed = 8 };
+
+// Warp partials of a CTA sum (up to three values per thread) and each
+// warp's vote.
+constexpr int kMaxSumValues = 3;
+struct SumScratch {
+  FxPart part[kMaxSumValues][kWarps];
+  int32_t ok[kWarps];
+};
+
 struct RingSmem {
   static constexpr int kRingAlloc = kRing + kMirror;
   static constexpr size_t kValBytes = sizeof(double) * kRingAlloc;
   static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc;
   static constexpr size_t kBarOff = (kValBytes + kColBytes + 15) & ~size_t(15);
-  static constexpr size_t kFxOff = kBarOff + 16 * kSlots;
-  static constexpr size_t kFxBytes = (sizeof(FxScratch) + 15) & ~size_t(15);
-  static constexpr size_t kMiscOff = kFxOff + kFxBytes;
+  static constexpr size_t kStateOff = kBarOff + 16 * kSlots;
+  static constexpr size_t kStateBytes = (sizeof(CtaState) + 15) & ~size_t(15);
+  static constexpr size_t kSumOff = kStateOff + kStateBytes;
+  static constexpr size_t kSumBytes = (sizeof(SumScratch) + 15) & ~size_t(15);
+  static constexpr size_t kMiscOff = kSumOff + kSumBytes;
   static constexpr size_t kBytes = kMiscOff + 64;
 
   unsigned char* base;
@@ -301,7 +416,8 @@ struct RingSmem {
   __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + kValBytes); }
   __device__ uint64_t* full(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + s; }
   __device__ uint64_t* empty(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots + s; }
-  __device__ FxScratch* fx() const { return reinterpret_cast<FxScratch*>(base + kFxOff); }
+  __device__ CtaState* state() const { return reinterpret_cast<CtaState*>(base + kStateOff); }
+  __device__ SumScratch* sums() const { return reinterpret_cast<SumScratch*>(base + kSumOff); }
   __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + kMiscOff); }
   __device__ int32_t* stop() const { return reinterpret_cast<int32_t*>(base + kMiscOff + 4); }
   __device__ double* scalars() const { return reinterpret_cast<double*>(base + kMiscOff + 16); }

@@ -25,9 +25,6 @@ __device__ __forceinline__ void solve_fail(const RingSmem& sm, const SolveParams
   if (threadIdx.x == 0) *reinterpret_cast<volatile int32_t*>(sm.stop()) = 1;
 }
 
-// CTA sums each thread reads in the grid-wide sum: nblocks <= kMaxCtaSums * kConsumers.
-constexpr int kMaxCtaSums = 2;
-
 // Producer side of a solve task: stream the CTA's share of the matrix (FP32
 // values in the mixed solve) pass after pass until the consumers stop it.
 template <bool kMixed>
@@ -48,139 +45,150 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
 // launch saved, for at most P.chunk_iters steps.
+//
+// Scalars live in the CTA state in shared memory (thread 0 updates them
+// between CTA barriers; every thread reads them after one), so that the
+// registers of the step loop's product are the product's own.
 template <bool kMixed, bool kJacobi>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
                                                 const int rank) {
   const DevCsr& A = P.A;
-  const int tid = threadIdx.x;
-  const unsigned long long lim = P.wait_limit_ns;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = A.block_row[rank], row1 = A.block_row[rank + 1];
-  int32_t* flag = sm.flag();
-  double* sc = sm.scalars();  // broadcast slots for per-step scalars
-  FxScratch* fx = sm.fx();
+  const int nb = P.group;
+  CtaState* st = sm.state();
+  SumScratch* ss = sm.sums();
   SolveCtrl* ctrl = P.ctrl;
-  const double* __restrict__ b = P.b;
   double* __restrict__ x = P.x;
   double* __restrict__ r = P.r;
   double* __restrict__ p = P.p;
-  double* __restrict__ q = P.q;
-  float* __restrict__ p32 = P.p32;
-  const double* __restrict__ dinv = P.dinv;  // Jacobi (kJacobi): z = dinv .* r; plain CG: z = r
-  const int nb = P.group;
   ConsumerCursor cur;
-  GridBarrier gb;
-  gb.count = static_cast<unsigned int>(nb);
-  int slot = 0;
-  int site = 0;
-  // state saved by an earlier launch of this solve (written by another
-  // kernel, so read through L2)
-  const int32_t phase0 = __ldcg(&ctrl->phase);
-  if (phase0 == kPhaseRunning) {
-    gb.target = __ldcg(&ctrl->rounds) * gb.count;
-    slot = __ldcg(&ctrl->slot);
-  }
 
-  // Group-wide sums of one or two values per thread, identical in every CTA.
-  // Each CTA sums its threads in fixed point, publishes the result, and after
-  // a group barrier every CTA sums the nb CTA values, again in fixed point
-  // (exact and order-independent, hence the same bits everywhere).  Two
-  // slots of partials (2 nb values each) alternate so that a fast CTA
-  // publishing the next sum never overwrites values a slow CTA is still
-  // reading.
-  auto group_sum = [&](const double* part) -> double {
-    double mine[kMaxCtaSums];
+  // Group-wide sum of nv values per thread (nv <= 3), fused with the vote of
+  // the consumer warps (`ok`: this thread's waits all succeeded).  Each warp
+  // sums its lanes exactly in fixed point; warp 0 combines the warps,
+  // publishes the CTA's values, meets the other CTAs of the group at the
+  // barrier and sums the group's CTA values in fixed point (exact and
+  // order-independent: the same bits in every CTA); lane 0 then runs
+  // fin(sums), which updates the CTA state; one CTA barrier publishes it.
+  // Two slots of partials (3 nb values each) alternate so that a fast CTA
+  // publishing the next sum never overwrites values a slow CTA still reads.
+  // Returns false in every thread if a wait gave up, here or anywhere before.
+  auto group_sum = [&](bool ok, int nv, double v0, double v1, double v2, auto&& fin) -> bool {
+    const double vin[kMaxSumValues] = {v0, v1, v2};
+    FxPart fp[kMaxSumValues];
 #pragma unroll
-    for (int j = 0; j < kMaxCtaSums; ++j) {
-      const int c = tid + j * kConsumers;
-      mine[j] = c < nb ? __ldcg(part + c) : 0.0;
+    for (int j = 0; j < kMaxSumValues; ++j)
+      if (j < nv) fp[j] = fx_warp(vin[j]);
+    const bool wok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < kMaxSumValues; ++j)
+        if (j < nv) ss->part[j][warp] = fp[j];
+      ss->ok[warp] = wok ? 1 : 0;
     }
-    return fx_block_sum<kMaxCtaSums>(mine, fx);
+    cta_sync();
+    if (warp == 0) {
+      const bool valid = lane < kWarps;
+      bool good = __all_sync(0xffffffffu, valid ? ss->ok[lane] != 0 : true);
+      double sum[kMaxSumValues] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < kMaxSumValues; ++j)
+        if (j < nv) sum[j] = fx_combine(valid ? ss->part[j][lane] : FxPart{0, 0, 0}, valid);
+      if (good && nb > 1) {
+        const int slot = st->slot;
+        double* part = P.partials + static_cast<size_t>(slot) * kMaxSumValues * nb;
+        int bar_ok = 1;
+        if (lane == 0) {
+#pragma unroll
+          for (int j = 0; j < kMaxSumValues; ++j)
+            if (j < nv) part[j * nb + rank] = sum[j];
+          bar_ok = group_barrier_t0(ctrl, &st->target, static_cast<unsigned int>(nb), P.wait_limit_ns, ++st->site);
+        }
+        good = __shfl_sync(0xffffffffu, bar_ok, 0) != 0;
+        __syncwarp();
+        if (good) {
+#pragma unroll
+          for (int j = 0; j < kMaxSumValues; ++j)
+            if (j < nv) sum[j] = fx_warp_sum_array(part + j * nb, nb);
+          if (lane == 0) st->slot = slot ^ 1;
+        }
+      }
+      if (lane == 0) {
+        st->ok = good ? 1 : 0;
+        if (good) fin(sum);
+      }
+    }
+    cta_sync();
+    return st->ok != 0;
   };
-  auto allreduce = [&](double v, double& out) -> bool {
-    const double cta = fx_block_sum(v, fx);
-    if (nb == 1) {  // a one-CTA group: the CTA sum is the sum
-      out = cta;
-      return true;
-    }
-    double* part = P.partials + static_cast<size_t>(slot) * 2 * nb;
-    if (tid == 0) part[rank] = cta;
-    if (!gb.sync(ctrl, lim, ++site, flag)) return false;
-    out = group_sum(part);
-    slot ^= 1;
-    return true;
+  // Group barrier of all threads: every write before it is visible to every
+  // CTA of the group after it.
+  auto group_sync = [&]() -> bool {
+    cta_sync();
+    if (tid == 0)
+      st->ok = group_barrier_t0(ctrl, &st->target, static_cast<unsigned int>(nb), P.wait_limit_ns, ++st->site) ? 1
+                                                                                                                : 0;
+    cta_sync();
+    return st->ok != 0;
   };
-  auto allreduce2 = [&](double v1, double v2, double& o1, double& o2) -> bool {
-    const double c1 = fx_block_sum(v1, fx);
-    const double c2 = fx_block_sum(v2, fx);
-    if (nb == 1) {
-      o1 = c1;
-      o2 = c2;
-      return true;
-    }
-    double* part = P.partials + static_cast<size_t>(slot) * 2 * nb;
-    if (tid == 0) {
-      part[rank] = c1;
-      part[nb + rank] = c2;
-    }
-    if (!gb.sync(ctrl, lim, ++site, flag)) return false;
-    o1 = group_sum(part);
-    o2 = group_sum(part + nb);
-    slot ^= 1;
-    return true;
-  };
-  // r.r and (Jacobi) r.z of per-thread partials: one sum without a
-  // preconditioner (r.z = r.r), both in one group barrier with one
-  auto sums_rr_rz = [&](double acc_rr, double acc_rz, double& rr, double& rz) -> bool {
-    if constexpr (kJacobi) {
-      return allreduce2(acc_rr, acc_rz, rr, rz);
-    } else {
-      if (!allreduce(acc_rr, rr)) return false;
-      rz = rr;
-      return true;
-    }
-  };
-  // The products outside the step loop (setup, true residual at the end,
-  // and the mixed solve's residual replacements) read the FP64 values and
-  // columns directly from global memory with a compact per-lane loop: they
-  // run once per solve (or once every replace_every steps), and keeping the
-  // large unrolled ring product out of them leaves its single copy, in the
-  // step loop, the registers it needs.  The ring keeps streaming the values
-  // the step loop uses.  Every product pass ends with a vote of all consumer
-  // warps, so that a warp that gave up on a wait and the others leave
-  // together.
+  // Products outside the step loop (setup, the final true residual, the
+  // mixed solve's residual replacements) read the FP64 values and columns
+  // directly from global memory with a compact per-lane loop: they run once
+  // per solve (or every replace_every steps), and keeping the unrolled ring
+  // product out of them leaves its single copy, in the step loop, the
+  // registers it needs.  The ring keeps streaming what the step loop uses.
   auto product64 = [&](const double* xin, const double* aux, auto& epi) -> bool {
-    const bool ok = spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, lim);
-    return cta_and(ok);
+    return spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, P.wait_limit_ns);
   };
 
-  // rho = r.z (the preconditioned inner product; r.r without a
-  // preconditioner), rr = r.r (the stopping test always uses ||r||)
-  double rho, bnorm2, rr;
-  int64_t k = 0;
-  if (phase0 == kPhaseRunning) {
-    rho = __ldcg(&ctrl->rho);
-    bnorm2 = __ldcg(&ctrl->bnorm2);
-    k = __ldcg(&ctrl->iters);
-    rr = __ldcg(&ctrl->relres_rec);
-    rr = rr * rr * bnorm2;
-  } else {
-    // ---- setup: r = b - A x, z = dinv .* r, p = z, rho = r.z, ||b||^2
+  // ---- state: saved by an earlier launch of this solve (written by another
+  // kernel, so read through L2), or fresh
+  if (tid == 0) {
+    st->slot = 0;
+    st->site = 0;
+    st->ok = 1;
+    st->flags = 0;
+    st->target = 0;
+    st->k = 0;
+    if (__ldcg(&ctrl->phase) == kPhaseRunning) {
+      st->target = __ldcg(&ctrl->rounds) * static_cast<unsigned long long>(nb);
+      st->slot = __ldcg(&ctrl->slot);
+      st->rho = __ldcg(&ctrl->rho);
+      st->bnorm2 = __ldcg(&ctrl->bnorm2);
+      st->k = __ldcg(&ctrl->iters);
+      const double rel = __ldcg(&ctrl->relres_rec);
+      st->rr = rel * rel * st->bnorm2;  // reported only (the next step recomputes it)
+      st->flags = kFlagResumed;
+    }
+  }
+  cta_sync();
+  if (!(st->flags & kFlagResumed)) {
+    // ---- setup: r = b - A x, z = dinv .* r (Jacobi) or r, p = z,
+    //      rho = r.z, rr = r.r, ||b||^2
     double acc_rr = 0.0, acc_bb = 0.0, acc_rz = 0.0;
     auto epi = [&](int i, double s, double bi) {
       const double ri = bi - s;
       double zi = ri;
-      if constexpr (kJacobi) zi = dinv[i] * ri;
+      if constexpr (kJacobi) zi = P.dinv[i] * ri;
       r[i] = ri;
       p[i] = zi;
-      if constexpr (kMixed) p32[i] = static_cast<float>(zi);
+      if constexpr (kMixed) P.p32[i] = static_cast<float>(zi);
       acc_rr = fma(ri, ri, acc_rr);
       if constexpr (kJacobi) acc_rz = fma(ri, zi, acc_rz);
       acc_bb = fma(bi, bi, acc_bb);
     };
-    if (!product64(x, b, epi)) { solve_fail(sm, P); return; }
-    if (!sums_rr_rz(acc_rr, acc_rz, rr, rho) || !allreduce(acc_bb, bnorm2)) { solve_fail(sm, P); return; }
+    const bool ok = product64(x, P.b, epi);
+    if (!group_sum(ok, kJacobi ? 3 : 2, acc_rr, acc_bb, acc_rz, [&](const double* sum) {
+          st->rr = sum[0];
+          st->bnorm2 = sum[1];
+          st->rho = kJacobi ? sum[2] : sum[0];
+        })) {
+      solve_fail(sm, P);
+      return;
+    }
   }
-  if (bnorm2 == 0.0) {  // b = 0: the solution is 0
+  if (st->bnorm2 == 0.0) {  // b = 0: the solution is 0
     for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = 0.0;
     if (rank == 0 && tid == 0) {
       ctrl->status = kOK;
@@ -194,125 +202,137 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     consumers_done(sm);
     return;
   }
-  // Stopping test sqrt(rho) <= tol ||b|| evaluated as rho <= tol^2 ||b||^2
-  // (no square root on the critical path; the same test up to rounding).
-  const double thresh2 = (P.tol * P.tol) * bnorm2;
-  const int64_t k_end = P.chunk_iters > 0 && P.chunk_iters < P.maxit - k ? k + P.chunk_iters : P.maxit;
-  int32_t status = kOK;
-  bool done = phase0 != kPhaseRunning && rr <= thresh2;
+  if (tid == 0) {
+    // Stopping test sqrt(rr) <= tol ||b|| evaluated as rr <= tol^2 ||b||^2
+    // (no square root on the critical path; the same test up to rounding).
+    st->thresh2 = (P.tol * P.tol) * st->bnorm2;
+    const long long k = st->k;
+    st->k_end = P.chunk_iters > 0 && P.chunk_iters < P.maxit - k ? k + P.chunk_iters : P.maxit;
+    if (!(st->flags & kFlagResumed) && st->rr <= st->thresh2) st->flags |= kFlagDone;
+  }
+  cta_sync();
 
-  while (!done && k < P.maxit) {
+  for (;;) {
+    if ((st->flags & kFlagDone) || st->k >= P.maxit) break;
     // ---- q = A p, gamma = p.q
     double acc_g = 0.0;
     bool ok;
     if constexpr (kMixed) {
       auto epi = [&](int i, float s, double pi) {
         const double qi = static_cast<double>(s);
-        q[i] = qi;
+        P.q[i] = qi;
         acc_g = fma(pi, qi, acc_g);
       };
-      ok = cta_and(spmv_pass<true, float, float, float>(sm, cs, cur, A, A.val32, p32, p, epi, lim));
+      ok = spmv_pass<true, float, float, float>(sm, cs, cur, A, A.val32, P.p32, p, epi, P.wait_limit_ns);
     } else {
       auto epi = [&](int i, double s, double pi) {
-        q[i] = s;
+        P.q[i] = s;
         acc_g = fma(pi, s, acc_g);
       };
-      ok = cta_and(spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, p, p, epi, lim));
+      ok = spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, p, p, epi, P.wait_limit_ns);
     }
-    double gamma;
-    if (!ok || !allreduce(acc_g, gamma)) { solve_fail(sm, P); return; }
-    if (!(gamma > 0.0) || !isfinite(gamma)) {  // not SPD, or overflow
-      status = kEBREAKDOWN;
-      break;
+    // alpha = rho / gamma, once per CTA (an FP64 division is slow)
+    if (!group_sum(ok, 1, acc_g, 0.0, 0.0, [&](const double* sum) {
+          const double gamma = sum[0];
+          if (!(gamma > 0.0) || !isfinite(gamma)) st->flags |= kFlagBreakdown;  // not SPD, or overflow
+          else st->alpha = st->rho / gamma;
+        })) {
+      solve_fail(sm, P);
+      return;
     }
-    // alpha = rho / gamma, computed once and broadcast (FP64 division is slow)
-    if (tid == 0) sc[0] = rho / gamma;
-    cta_sync();
-    const double alpha = sc[0];
+    if (st->flags & kFlagBreakdown) break;
+    const double alpha = st->alpha;
 
-    // ---- r -= alpha q, rr' = r.r, rho' = r.z   (four rows per thread in flight)
+    // ---- r -= alpha q; rr = r.r and (Jacobi) r.z   (four rows per thread in flight)
     double acc_r = 0.0, acc_z = 0.0;
-    {
-      constexpr bool jac = kJacobi;
-      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-        double qv[4], rv[4], dv[4];
+    for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
+      double qv[4], rv[4], dv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = base + u * kConsumers;
-          if (i < row1) {
-            qv[u] = q[i];
-            rv[u] = r[i];
-            if constexpr (jac) dv[u] = dinv[i];
-          }
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * kConsumers;
+        if (i < row1) {
+          qv[u] = P.q[i];
+          rv[u] = r[i];
+          if constexpr (kJacobi) dv[u] = P.dinv[i];
         }
+      }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = base + u * kConsumers;
-          if (i < row1) {
-            const double rn = fma(-alpha, qv[u], rv[u]);
-            r[i] = rn;
-            acc_r = fma(rn, rn, acc_r);
-            if constexpr (jac) acc_z = fma(rn, dv[u] * rn, acc_z);
-          }
+      for (int u = 0; u < 4; ++u) {
+        const int i = base + u * kConsumers;
+        if (i < row1) {
+          const double rn = fma(-alpha, qv[u], rv[u]);
+          r[i] = rn;
+          acc_r = fma(rn, rn, acc_r);
+          if constexpr (kJacobi) acc_z = fma(rn, dv[u] * rn, acc_z);
         }
       }
     }
-    double rho_new;
-    if (!sums_rr_rz(acc_r, acc_z, rr, rho_new)) { solve_fail(sm, P); return; }
-    ++k;
-
-    bool replace = false;
-    if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rr <= thresh2;
-    if (replace) {
-      // x += alpha p, then r = b - A x in FP64 (residual replacement).  The
-      // direction keeps the recurrence's beta = rho_rec / rho (rho_rec: the
-      // recursive r.z of this step); r, rr and rho take the true residual's
-      // values.
-      if (tid == 0) sc[1] = rho_new / rho;
+    if (!group_sum(true, kJacobi ? 2 : 1, acc_r, acc_z, 0.0, [&](const double* sum) {
+          const long long k = st->k + 1;
+          st->k = k;
+          const double rr = sum[0], rho_new = kJacobi ? sum[1] : sum[0];
+          st->rr = rr;
+          // beta keeps the recurrence's own ratio (rho_new: the recursive r.z
+          // of this step), also when r is replaced below
+          st->beta = rho_new / st->rho;
+          bool replace = false;
+          if constexpr (kMixed) replace = (P.replace_every > 0 && k % P.replace_every == 0) || rr <= st->thresh2;
+          if (replace) {
+            st->flags |= kFlagReplace;
+          } else {
+            if (rr <= st->thresh2) st->flags |= kFlagDone;
+            st->rho = rho_new;
+          }
+        })) {
+      solve_fail(sm, P);
+      return;
+    }
+    const int32_t f = st->flags;
+    const double beta = st->beta;
+    if (f & kFlagReplace) {
+      // x += alpha p, then r = b - A x in FP64 (residual replacement); r, rr
+      // and rho take the true residual's values
       for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
-      if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
-      const double beta = sc[1];
+      if (!group_sync()) { solve_fail(sm, P); return; }
       double acc_t = 0.0, acc_tz = 0.0;
       auto epi = [&](int i, double s, double bi) {
         const double ri = bi - s;
         r[i] = ri;
         acc_t = fma(ri, ri, acc_t);
-        if constexpr (kJacobi) acc_tz = fma(ri, dinv[i] * ri, acc_tz);
+        if constexpr (kJacobi) acc_tz = fma(ri, P.dinv[i] * ri, acc_tz);
       };
-      if (!product64(x, b, epi) || !sums_rr_rz(acc_t, acc_tz, rr, rho_new)) { solve_fail(sm, P); return; }
-      if (rr <= thresh2) {
-        rho = rho_new;
-        done = true;
-        break;
+      const bool okr = product64(x, P.b, epi);
+      if (!group_sum(okr, kJacobi ? 2 : 1, acc_t, acc_tz, 0.0, [&](const double* sum) {
+            st->rr = sum[0];
+            st->rho = kJacobi ? sum[1] : sum[0];
+            st->flags &= ~kFlagReplace;
+            if (sum[0] <= st->thresh2) st->flags |= kFlagDone;
+          })) {
+        solve_fail(sm, P);
+        return;
       }
+      if (st->flags & kFlagDone) break;
       for (int i = row0 + tid; i < row1; i += kConsumers) {
         double zi = r[i];
-        if constexpr (kJacobi) zi = dinv[i] * zi;
+        if constexpr (kJacobi) zi = P.dinv[i] * zi;
         const double pi = fma(beta, p[i], zi);
         p[i] = pi;
-        if constexpr (kMixed) p32[i] = static_cast<float>(pi);
+        if constexpr (kMixed) P.p32[i] = static_cast<float>(pi);
       }
-      rho = rho_new;
+    } else if (f & kFlagDone) {
+      for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
+      break;
     } else {
-      if (!kMixed && rr <= thresh2) {
-        for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
-        rho = rho_new;
-        done = true;
-        break;
-      }
       // ---- x += alpha p; p = z + beta p   (z = dinv .* r, or r)
-      if (tid == 0) sc[1] = rho_new / rho;
-      cta_sync();
-      const double beta = sc[1];
       for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-        double pv[4], rv[4], xv[4];
+        double pv[4], zv[4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
             pv[u] = p[i];
-            rv[u] = r[i];
-            if constexpr (kJacobi) rv[u] = dinv[i] * rv[u];
+            zv[u] = r[i];
+            if constexpr (kJacobi) zv[u] = P.dinv[i] * zv[u];
             xv[u] = x[i];
           }
         }
@@ -321,53 +341,53 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           const int i = base + u * kConsumers;
           if (i < row1) {
             x[i] = fma(alpha, pv[u], xv[u]);
-            const double pn = fma(beta, pv[u], rv[u]);
+            const double pn = fma(beta, pv[u], zv[u]);
             p[i] = pn;
-            if constexpr (kMixed) p32[i] = static_cast<float>(pn);
+            if constexpr (kMixed) P.p32[i] = static_cast<float>(pn);
           }
         }
       }
-      rho = rho_new;
     }
-    if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
-    if (k >= k_end && k < P.maxit) {
-      // end of this launch's share of the solve: save the state (identical
-      // in every CTA of the group; x, r, p are complete after the barrier)
+    if (!group_sync()) { solve_fail(sm, P); return; }
+    if (st->k >= st->k_end && st->k < P.maxit) {
+      // end of this launch's share of the solve: save the state (identical in
+      // every CTA of the group; x, r, p are complete after the barrier)
       if (rank == 0 && tid == 0) {
-        ctrl->iters = k;
-        ctrl->rho = rho;
-        ctrl->bnorm2 = bnorm2;
-        ctrl->relres_rec = sqrt(rr / bnorm2);
-        ctrl->rounds = gb.target / gb.count;
-        ctrl->slot = slot;
+        ctrl->iters = st->k;
+        ctrl->rho = st->rho;
+        ctrl->bnorm2 = st->bnorm2;
+        ctrl->relres_rec = sqrt(st->rr / st->bnorm2);
+        ctrl->rounds = st->target / static_cast<unsigned long long>(nb);
+        ctrl->slot = st->slot;
         ctrl->phase = kPhaseRunning;
       }
       consumers_done(sm);
       return;
     }
   }
-  if (status == kOK && !done) status = kENOTCONV;
 
   // ---- true residual ||b - A x|| / ||b|| (x complete everywhere first)
-  if (!gb.sync(ctrl, lim, ++site, flag)) { solve_fail(sm, P); return; }
+  if (!group_sync()) { solve_fail(sm, P); return; }
   double acc_t = 0.0;
-  {
-    auto epi = [&](int i, double s, double bi) {
-      const double d = bi - s;
-      acc_t = fma(d, d, acc_t);
-    };
-    double tsum;
-    if (!product64(x, b, epi) || !allreduce(acc_t, tsum)) { solve_fail(sm, P); return; }
-    acc_t = tsum;
-  }
-  if (rank == 0 && tid == 0) {
-    ctrl->status = status;
-    ctrl->iters = k;
-    ctrl->rho = rho;
-    ctrl->bnorm2 = bnorm2;
-    ctrl->relres_rec = sqrt(rr / bnorm2);
-    ctrl->relres_true = sqrt(acc_t / bnorm2);
-    ctrl->phase = kPhaseDone;
+  auto epi = [&](int i, double s, double bi) {
+    const double d = bi - s;
+    acc_t = fma(d, d, acc_t);
+  };
+  const bool okt = product64(x, P.b, epi);
+  if (!group_sum(okt, 1, acc_t, 0.0, 0.0, [&](const double* sum) {
+        if (rank == 0) {
+          const int32_t f = st->flags;
+          ctrl->status = (f & kFlagBreakdown) ? kEBREAKDOWN : ((f & kFlagDone) ? kOK : kENOTCONV);
+          ctrl->iters = st->k;
+          ctrl->rho = st->rho;
+          ctrl->bnorm2 = st->bnorm2;
+          ctrl->relres_rec = sqrt(st->rr / st->bnorm2);
+          ctrl->relres_true = sqrt(sum[0] / st->bnorm2);
+          ctrl->phase = kPhaseDone;
+        }
+      })) {
+    solve_fail(sm, P);
+    return;
   }
   consumers_done(sm);
 }
