@@ -796,8 +796,10 @@ def run_serve(args):
             "note": "single FIFO server of cg_solve (FP64, whole GPU per solve): measured service time per "
                     "(edge, rhs) pair applied to the same arrival times"}
 
+    jac = args.precond == "jacobi"
     bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=args.chunk,
-                  validate=False, budget_bytes=int(args.budget_gb * 2**30), max_systems=1024)
+                  validate=False, budget_bytes=int(args.budget_gb * 2**30), max_systems=1024,
+                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
     outs = [torch.zeros(pool[int(N)]["n"], dtype=torch.float64, device=dev) for N in edges]
     reqs = [cg.Request(pool[int(N)]["rp"], pool[int(N)]["ci"], pool[int(N)]["va"], pool[int(N)]["b"][i % 4],
                        outs[i], tol=TOL, maxit=10 * pool[int(N)]["n"], tag=i) for i, N in enumerate(edges)]
@@ -840,8 +842,8 @@ def run_serve(args):
     last = max(r.done_ms for r in res)
     value = count / ((last - first) / 1000.0)
     dev_s = (st1["round_ms_total"] - st0["round_ms_total"]) / 1000.0
-    bytes_all = sum(solve_bytes(pool[int(edges[r.tag])]["n"], pool[int(edges[r.tag])]["nnz"], r.iters, mixed)
-                    for r in res)
+    bytes_all = sum(solve_bytes(pool[int(edges[r.tag])]["n"], pool[int(edges[r.tag])]["nnz"], r.iters, mixed,
+                                jacobi=jac) for r in res)
     hbm_peak, peak_kind = peaks()
     achieved = bytes_all / dev_s / 1e9
     line = {
@@ -850,7 +852,8 @@ def run_serve(args):
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"served stream: Poisson arrivals at {args.serve_rate:g} req/s for "
                                f"{args.serve_seconds:g} s, Q1 27-point FE systems with grid edge lognormal in "
-                               f"[16, 96], {'mixed precision' if mixed else 'FP64'}, CG to 1e-10, "
+                               f"[16, 96], {'mixed precision' if mixed else 'FP64'}, "
+                               f"{'Jacobi-preconditioned ' if jac else ''}CG to 1e-10, "
                                f"{args.budget_gb:g} GB device budget, {args.chunk} steps per system per round",
                    "requests": count, "distinct_edges": len(pool), "rhs_per_edge": 4,
                    "mean_nnz": float(np.mean([pool[int(N)]["nnz"] for N in edges]))},
@@ -864,7 +867,7 @@ def run_serve(args):
         "speedup_vs_fp64_fifo": value / fifo["solves_per_s"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
-                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}, false>",
+                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>",
                      "device_busy_frac": dev_s / t_end},
         "energy": {"joules_per_solve": (j1 - j0) / count if j0 is not None and j1 is not None else None,
                    "fp64_fifo_joules_per_solve": None, "source": "NVML board energy over the whole stream"},
