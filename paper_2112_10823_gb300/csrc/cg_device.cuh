@@ -273,20 +273,25 @@ __device__ __forceinline__ double fx_warp_sum_array(const double* src, int count
 
 // Arrival and bounded wait of thread 0 at the group barrier of a system
 // (the caller synchronises its own CTA around it).  `target` is the CTA's
-// running target (in shared memory: thread 0 alone keeps it).  Returns false
-// after a wait longer than limit_ns or an abort raised by another CTA.
+// running target (in shared memory: thread 0 alone keeps it).  The arrival is
+// a release pattern (an acq_rel fence, cumulative over what the CTA wrote
+// before the CTA barrier that precedes it, then a relaxed add); the wait
+// polls with relaxed loads and ends with an acquire pattern (an acq_rel
+// fence).  These fences are lighter than the sequentially consistent one of
+// __threadfence().  Returns false after a wait longer than limit_ns or an
+// abort raised by another CTA.
 __device__ __forceinline__ bool group_barrier_t0(SolveCtrl* ctrl, unsigned long long* target, unsigned int count,
                                                  unsigned long long limit_ns, int site) {
   *target += count;
   if (count <= 1) return true;
-  __threadfence();
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctrl->barrier), "l"(1ull) : "memory");
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(&ctrl->barrier), "l"(1ull) : "memory");
   unsigned long long t0 = 0;
   uint32_t spins = 0;
   const unsigned long long tgt = *target;
   for (;;) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&ctrl->barrier) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&ctrl->barrier) : "memory");
     if (v >= tgt) break;
     if ((++spins & 255u) == 0) {
       if (*reinterpret_cast<const volatile int32_t*>(&ctrl->abort)) return false;
@@ -299,7 +304,7 @@ __device__ __forceinline__ bool group_barrier_t0(SolveCtrl* ctrl, unsigned long 
       }
     }
   }
-  __threadfence();
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
   return true;
 }
 
