@@ -249,3 +249,34 @@ def test_groups_beyond_one_wave():
     for (A, b), req, r in zip(systems, reqs, res):
         assert r.group == min(100, st["nblocks"])
         _check_vs_oracle(A, b, r, _x(req))
+
+
+def test_served_request_joins_running_rounds_with_the_same_bits():
+    """Continuous batching: a request submitted while other systems are part
+    way through their solves (rounds of a few steps) is admitted at a later
+    round, overlaps them on the device, and gives exactly the bits it gives
+    when it runs alone."""
+    import time
+    cg = cg_mod()
+    A, b = _system(11, 1200)
+    others = [_system(N, 1210 + N) for N in (18, 20, 22)]
+    with cg.Batch(chunk_iters=4) as bt:
+        r_alone = _request(A, b)
+        ra = _wait1(bt, bt.submit([r_alone])[0])
+        r0 = bt.stats()["rounds"]
+        reqs = [_request(*s) for s in others]
+        tick = bt.submit(reqs)
+        t0 = time.time()
+        while bt.stats()["rounds"] < r0 + 3 and time.time() - t0 < 60:
+            time.sleep(0.001)
+        late = _request(A, b)
+        tl = bt.submit([late])[0]
+        res = _wait_all(bt, tick + [tl])
+    rl = res[-1]
+    assert ra.status == rl.status == cg.CG_OK
+    assert rl.iters == ra.iters and np.array_equal(_x(r_alone), _x(late))
+    # it joined while the others were running and finished among them
+    assert rl.admit_ms > min(r.admit_ms for r in res[:-1])
+    assert rl.admit_ms < max(r.done_ms for r in res[:-1])
+    for (S, bs), req, r in zip(others, reqs, res[:-1]):
+        _check_vs_oracle(S, bs, r, _x(req))
