@@ -72,6 +72,10 @@ def parse(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the arrival window")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="device memory budget of the server")
     ap.add_argument("--chunk", type=int, default=50, help="serve: steps per system per round")
+    ap.add_argument("--no-autotune", action="store_true", help="batch/serve: built-in group-size model")
+    ap.add_argument("--group-target-ms", type=int, default=50, help="batch/serve: solo time a group aims at")
+    ap.add_argument("--matrix", default="q1", choices=["q1", "lap7"],
+                    help="q1: the Q1 FE system (default); lap7: the 7-point Laplacian (with --grid 16: n = 4096)")
     ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
                     help="none: the paper's plain CG; jacobi: preconditioned by diag(A)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
@@ -285,9 +289,9 @@ class Energy:
 
 # ----------------------------------------------------------------- workload
 
-def make_problem(seed: int, grid: int = GRID_N):
+def make_problem(seed: int, grid: int = GRID_N, matrix: str = "q1"):
     import fe_inputs as fi
-    A = fi.q1(grid, SIGMA, seed)
+    A = fi.q1(grid, SIGMA, seed) if matrix == "q1" else fi.laplace7(grid)
     xs = fi.xstar(seed, A.n)
     return A, xs
 
@@ -319,9 +323,11 @@ def whole_job_rate(steps: int, world: int, t_max: float) -> float:
     return steps * world / t_max
 
 
-def workload_name(grid: int, precision: str, precond: str = "none") -> str:
+def workload_name(grid: int, precision: str, precond: str = "none", matrix: str = "q1") -> str:
     prec = "FP64 CSR" if precision == "fp64" else "FP32-value product with FP64 residual replacement every 50 steps"
     method = "CG" if precond == "none" else "Jacobi-preconditioned CG"
+    if matrix == "lap7":
+        return f"3-D 7-point Laplacian, {grid}^3 grid, Dirichlet, {prec}, x* ~ U(-1,1), {method} from x0 = 0 to 1e-10"
     return f"Q1 27-point FE, {grid}^3 grid, lognormal rho (sigma=1), {prec}, {method} to 1e-10"
 
 
@@ -372,7 +378,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    A, xs = make_problem(args.seed, args.grid)
+    A, xs = make_problem(args.seed, args.grid, args.matrix)
     b = oracle.spmv(A, xs)
     times, iters, sample = [], 0, ""
     # a full solve per step where it takes seconds; a bounded sample otherwise
@@ -398,7 +404,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.grid, args.precision, args.precond),
+        "config": {"workload": workload_name(args.grid, args.precision, args.precond, args.matrix),
                    "n": A.n, "nnz": A.nnz, "iters": iters, "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -419,7 +425,7 @@ def run_ours(args):
     import paper_2112_10823_gb300 as cg
 
     seed = replica_seed(args.seed, rank)
-    A, xs = make_problem(seed, args.grid)
+    A, xs = make_problem(seed, args.grid, args.matrix)
     n, nnz = A.n, A.nnz
     stream = torch.cuda.current_stream(dev)
     rp = torch.from_numpy(A.row_ptr).to(dev)
@@ -542,7 +548,7 @@ def run_ours(args):
     achieved_gbs = bytes_launch / launch_s / 1e9
     achieved_gflops = flops_launch / launch_s / 1e9
     kname = f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>"
-    traffic = recorded_traffic(kname, f"q1_{args.grid}")
+    traffic = recorded_traffic(kname, f"{args.matrix}_{args.grid}")
     if l2_resident(n, nnz, mixed) or not mixed and achieved_gflops / FP64_PEAK_GFLOPS > achieved_gbs / hbm_peak:
         # the system stays in L2 during a solve (or the FP64 pipe is nearer its
         # peak than HBM is): the FP64 pipe bounds the kernel
@@ -569,7 +575,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.grid, args.precision, args.precond),
+        "config": {"workload": workload_name(args.grid, args.precision, args.precond, args.matrix),
                    "n": n, "nnz": nnz, "iters": iters, "tol": TOL, "x0": "zero",
                    "l2": "flushed before every timed solve (256 MiB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -671,7 +677,10 @@ def run_batch(args):
     jac = args.precond == "jacobi"
     bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=0, validate=False,
                   budget_bytes=int(args.budget_gb * 2**30), max_systems=max(1024, count),
-                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
+                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE, autotune=not args.no_autotune,
+                  group_target_ms=args.group_target_ms)
+    model = {k: bt.stats()[k] for k in ("autotuned", "cta_bytes_per_s", "group_cta_bytes_per_s", "step_overhead_s",
+                                        "group_step_overhead_s")}
 
     def step():
         reqs = [cg.Request(s["rp"], s["ci"], s["va"], s["b"], s["x"], tol=TOL, maxit=10 * s["n"], tag=i)
@@ -716,7 +725,7 @@ def run_batch(args):
                    "systems": count, "sum_n": int(sum(s["n"] for s in systems)),
                    "sum_nnz": int(sum(s["nnz"] for s in systems)), "iters_min": min(iters), "iters_max": max(iters),
                    "groups": {str(g): groups.count(g) for g in sorted(set(groups))},
-                   "rounds_per_step": rounds / args.steps, "graph": bool(st1["graph"]),
+                   "rounds_per_step": rounds / args.steps, "graph": bool(st1["graph"]), "group_model": model,
                    "l2": "flushed before every step (256 MiB write); the batch's matrices exceed L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_kind,
@@ -799,7 +808,8 @@ def run_serve(args):
     jac = args.precond == "jacobi"
     bt = cg.Batch(precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64, chunk_iters=args.chunk,
                   validate=False, budget_bytes=int(args.budget_gb * 2**30), max_systems=1024,
-                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
+                  preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE, autotune=not args.no_autotune,
+                  group_target_ms=args.group_target_ms)
     outs = [torch.zeros(pool[int(N)]["n"], dtype=torch.float64, device=dev) for N in edges]
     reqs = [cg.Request(pool[int(N)]["rp"], pool[int(N)]["ci"], pool[int(N)]["va"], pool[int(N)]["b"][i % 4],
                        outs[i], tol=TOL, maxit=10 * pool[int(N)]["n"], tag=i) for i, N in enumerate(edges)]

@@ -217,7 +217,10 @@ int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status);
  * precision (x0 = 0; the same stopping test and outputs).  How many CTAs
  * solve a system (its "group") is chosen from the system alone (its rows,
  * entries and row lengths), never from the rest of the batch, so a system
- * gives the same bits alone and in any mix on the same batch object.
+ * gives the same bits alone and in any mix on the same batch object.  The
+ * choice is the smallest group whose estimated solo solve time meets
+ * group_target_ms under a cost model (per-CTA streaming rate and per-step overheads) that
+ * cg_batch_opts.autotune measures on the GPU at creation.
  * ---------------------------------------------------------------------- */
 
 typedef struct cg_batch_ctx* cg_batch;
@@ -237,7 +240,12 @@ typedef struct {
   int32_t validate;        /* 1 (default): check each request's CSR on the host */
   int32_t preconditioner;  /* cg_preconditioner of every system (a non-positive diagonal
                               ends that request with CG_EINVAL) */
-  int32_t reserved[5];     /* zero */
+  int32_t autotune;        /* 1: measure the group-size cost model on this GPU at creation
+                              (a few rounds of synthetic systems, well under a second);
+                              0 (default): built-in constants */
+  int32_t group_target_ms; /* solo solve time the automatic group size aims at (default 50:
+                              smaller favours latency, larger favours throughput) */
+  int32_t reserved[3];     /* zero */
 } cg_batch_opts;
 
 /* One system to solve: A x = b from x0 = 0. */
@@ -276,6 +284,14 @@ typedef struct {
   int32_t nblocks;         /* CTAs of the persistent kernel */
   double round_ms_total;   /* device time of all rounds (CUDA events around each) */
   double last_round_ms;    /* device time of the last round */
+  /* cost model of the automatic group size (measured if autotuned): a step of
+   * a system on G CTAs takes bytes_per_step / (G * cta_bytes_per_s) + overhead */
+  double cta_bytes_per_s;          /* one CTA's streaming rate with every SM busy, G = 1 */
+  double group_cta_bytes_per_s;    /* the same inside a group of several CTAs */
+  double step_overhead_s;          /* per step, G = 1 */
+  double group_step_overhead_s;    /* per step, G > 1 */
+  int32_t autotuned;               /* 1 if the model was measured */
+  int32_t pad;
 } cg_batch_stats;
 
 /* Fill *o with the defaults above. */

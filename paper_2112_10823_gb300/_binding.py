@@ -45,7 +45,8 @@ class cg_batch_opts(ctypes.Structure):
                 ("replace_every", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
                 ("max_pending", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("group_override", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("preconditioner", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("preconditioner", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("group_target_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class cg_request(ctypes.Structure):
@@ -66,7 +67,9 @@ class cg_batch_stats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("resident", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
                 ("graph", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("round_ms_total", ctypes.c_double),
-                ("last_round_ms", ctypes.c_double)]
+                ("last_round_ms", ctypes.c_double), ("cta_bytes_per_s", ctypes.c_double),
+                ("group_cta_bytes_per_s", ctypes.c_double), ("step_overhead_s", ctypes.c_double),
+                ("group_step_overhead_s", ctypes.c_double), ("autotuned", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -391,7 +394,8 @@ class Batch:
     def __init__(self, precision: int = CG_PREC_FP64, budget_bytes: int = 0, max_systems: int = 1024,
                  chunk_iters: int = 0, replace_every: int = 50, wait_limit_ms: int = 2000,
                  max_pending: int = 65536, use_graph: bool = True, group_override: int = 0,
-                 validate: bool = True, device: int = -1, preconditioner: int = CG_PRECOND_NONE):
+                 validate: bool = True, device: int = -1, preconditioner: int = CG_PRECOND_NONE,
+                 autotune: bool = False, group_target_ms: int = 50):
         o = cg_batch_opts()
         lib.cg_batch_opts_default(ctypes.byref(o))
         o.device, o.precision, o.budget_bytes = int(device), int(precision), int(budget_bytes)
@@ -399,6 +403,8 @@ class Batch:
         o.wait_limit_ms, o.max_pending, o.use_graph = int(wait_limit_ms), int(max_pending), 1 if use_graph else 0
         o.group_override, o.validate = int(group_override), 1 if validate else 0
         o.preconditioner = int(preconditioner)
+        o.autotune = 1 if autotune else 0
+        o.group_target_ms = int(group_target_ms)
         out = ctypes.c_void_p(0)
         st = lib.cg_batch_create(ctypes.byref(out), ctypes.byref(o))
         if st != CG_OK:

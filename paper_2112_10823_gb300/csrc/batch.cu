@@ -86,16 +86,18 @@ class Arena {
 };
 
 // Cost model behind the automatic group size.  A system's solve on G CTAs
-// is estimated as steps * (bytes_per_step / (G * cta_rate) + overhead_G); the
+// is estimated as steps * (bytes_per_step / (G * rate_G) + overhead_G); the
 // group is the smallest G whose estimate meets target_s.  The step count of
 // a 3-D finite-element system grows like n^(1/3) (CG's step count follows
-// sqrt(condition number), which grows like h^-1).
+// sqrt(condition number), which grows like h^-1).  The rates and overheads
+// are built-in guesses unless measured on the GPU (calibrate() below).
 struct GroupModel {
-  double cta_rate = 40e9;        // bytes/s one CTA streams while every SM is busy
+  double cta_rate = 40e9;        // bytes/s one CTA streams while every SM is busy (G = 1)
+  double group_rate = 40e9;      // the same for a CTA inside a group (G > 1)
   double overhead_1 = 3e-6;      // s per step of a one-CTA group (CTA barriers, sums)
   double overhead_g = 8e-6;      // s per step of a multi-CTA group (group barriers)
   double steps_per_cbrt_n = 6.2; // estimated steps / n^(1/3)
-  double target_s = 20e-3;       // solo solve time a group should meet
+  double target_s = 50e-3;       // solo solve time a group should meet
 };
 
 double est_steps(const GroupModel& m, int64_t n) { return m.steps_per_cbrt_n * std::cbrt(static_cast<double>(n)); }
@@ -110,7 +112,8 @@ int auto_group(const GroupModel& m, int64_t n, int64_t nnz, bool mixed, int nblo
                                                            n / 4096}));
   const double steps = est_steps(m, n), bs = bytes_per_step(n, nnz, mixed);
   for (int g = 1; g <= gmax; ++g) {
-    const double t = steps * (bs / (g * m.cta_rate) + (g == 1 ? m.overhead_1 : m.overhead_g));
+    const double t = g == 1 ? steps * (bs / m.cta_rate + m.overhead_1)
+                            : steps * (bs / (g * m.group_rate) + m.overhead_g);
     if (t <= m.target_s) return g;
   }
   return gmax;
@@ -171,6 +174,8 @@ struct cg_batch_ctx {
   unsigned long long wait_ns = 2000000000ull;
   int max_pending = 65536;
   int group_override = 0;
+  int calib_group = 0;        // group of the calibration requests (while calibrating)
+  bool autotuned = false;
   bool validate = true;
   int nblocks = 0;
   int task_cap = 0;
@@ -366,8 +371,9 @@ void admit(cg_batch_ctx* b) {
       continue;
     }
     const int64_t n = r.n, nnz = r.nnz;
-    const int group = b->group_override > 0 ? std::min(b->group_override, b->nblocks)
-                                            : auto_group(b->model, n, nnz, b->mixed, b->nblocks);
+    const int group = b->calib_group > 0      ? std::min(b->calib_group, b->nblocks)
+                      : b->group_override > 0 ? std::min(b->group_override, b->nblocks)
+                                              : auto_group(b->model, n, nnz, b->mixed, b->nblocks);
     cgh::Partition part;
     cgh::build_partition(rp, n, group, part);
     const Layout L = layout_of(n, nnz, part.step.size(), group, b->mixed, b->jacobi);
@@ -677,6 +683,123 @@ bool request_ok(const cg_request& r, std::string& why) {
   return why.empty();
 }
 
+// 27-point stencil on an m^3 grid, boundary eliminated: diagonal 27, each
+// of the (up to) 26 neighbours -1 (strictly diagonally dominant, hence SPD).
+// A timing workload of the calibration only.
+void stencil27(int m, std::vector<int32_t>& rp, std::vector<int32_t>& ci, std::vector<double>& va) {
+  const int64_t n = static_cast<int64_t>(m) * m * m;
+  rp.assign(static_cast<size_t>(n) + 1, 0);
+  ci.clear();
+  va.clear();
+  for (int z = 0; z < m; ++z)
+    for (int y = 0; y < m; ++y)
+      for (int x = 0; x < m; ++x) {
+        const int64_t i = (static_cast<int64_t>(z) * m + y) * m + x;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int zz = z + dz, yy = y + dy, xx = x + dx;
+              if (zz < 0 || yy < 0 || xx < 0 || zz >= m || yy >= m || xx >= m) continue;
+              const int64_t j = (static_cast<int64_t>(zz) * m + yy) * m + xx;
+              ci.push_back(static_cast<int32_t>(j));
+              va.push_back(j == i ? 27.0 : -1.0);
+            }
+        rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(ci.size());
+      }
+}
+
+// Device time per step when `copies` copies of one system are solved
+// together, each by `group` CTAs, for exactly `steps` steps (tol 0).  < 0 if
+// they do not fit the budget at once or a request failed.
+double time_per_step(cg_batch_ctx* b, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
+                     const std::vector<double>& va, int copies, int group, int steps) {
+  const int64_t n = static_cast<int64_t>(rp.size()) - 1, nnz = static_cast<int64_t>(ci.size());
+  if (copies <= 0 || static_cast<size_t>(copies) * footprint_bound(n, nnz, b->mixed, b->jacobi, b->nblocks) >
+                         b->arena.cap() ||
+      copies > b->max_systems)
+    return -1.0;
+  std::vector<double> bv(static_cast<size_t>(n), 1.0);
+  std::vector<std::vector<double>> xs(static_cast<size_t>(copies), std::vector<double>(static_cast<size_t>(n)));
+  std::vector<cg_request> reqs(static_cast<size_t>(copies));
+  for (int i = 0; i < copies; ++i) {
+    cg_request& r = reqs[static_cast<size_t>(i)];
+    std::memset(&r, 0, sizeof(r));
+    r.csr.row_ptr = rp.data();
+    r.csr.col_idx = ci.data();
+    r.csr.val = va.data();
+    r.n = n;
+    r.nnz = nnz;
+    r.b = bv.data();
+    r.x = xs[static_cast<size_t>(i)].data();
+    r.tol = 0.0;
+    r.maxit = steps;
+  }
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->calib_group = group;
+  }
+  cg_batch_stats s0, s1;
+  cg_batch_get_stats(b, &s0);
+  std::vector<uint64_t> tickets(static_cast<size_t>(copies));
+  bool ok = cg_batch_submit(b, reqs.data(), copies, tickets.data()) == CG_OK;
+  for (size_t i = 0; ok && i < tickets.size(); ++i) {
+    cg_result r;
+    if (cg_batch_wait(b, tickets[i], 60000, &r) != CG_OK || !r.done || (r.status != CG_OK && r.status != CG_ENOTCONV))
+      ok = false;
+  }
+  cg_batch_get_stats(b, &s1);
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->calib_group = 0;
+  }
+  if (!ok) return -1.0;
+  return (s1.round_ms_total - s0.round_ms_total) * 1e-3 / steps;
+}
+
+// The autotuner of the group size: measure the cost model's rates and
+// per-step overheads on this GPU with synthetic 27-point systems, all CTAs
+// busy.  One-CTA systems of two sizes give the rate and overhead of G = 1
+// (time per step = bytes / rate + overhead); one size solved by groups of 8
+// and of 16 CTAs gives those of groups.  Any measurement that fails or is
+// inconsistent keeps the built-in value.
+void calibrate(cg_batch_ctx* b) {
+  std::vector<int32_t> rp0, ci0, rp1, ci1, rp2, ci2;
+  std::vector<double> va0, va1, va2;
+  stencil27(10, rp0, ci0, va0);
+  stencil27(20, rp1, ci1, va1);
+  stencil27(40, rp2, ci2, va2);
+  constexpr int kSteps = 40;
+  const double t0 = time_per_step(b, rp0, ci0, va0, b->nblocks, 1, kSteps);
+  const double t1 = time_per_step(b, rp1, ci1, va1, b->nblocks, 1, kSteps);
+  const double t8 = time_per_step(b, rp2, ci2, va2, b->nblocks / 8, 8, kSteps);
+  const double t16 = time_per_step(b, rp2, ci2, va2, b->nblocks / 16, 16, kSteps);
+  auto bytes = [&](const std::vector<int32_t>& rp, const std::vector<int32_t>& ci) {
+    return bytes_per_step(static_cast<int64_t>(rp.size()) - 1, static_cast<int64_t>(ci.size()), b->mixed);
+  };
+  const double B0 = bytes(rp0, ci0), B1 = bytes(rp1, ci1), B2 = bytes(rp2, ci2);
+  GroupModel m = b->model;
+  bool got1 = false, got_g = false;
+  if (t0 > 0 && t1 > t0) {
+    const double rate = (B1 - B0) / (t1 - t0), ov = t0 - B0 / rate;
+    if (rate > 0 && ov >= 0) {
+      m.cta_rate = rate;
+      m.overhead_1 = ov;
+      got1 = true;
+    }
+  }
+  if (t8 > 0 && t16 > 0 && t8 > t16) {
+    const double rate = B2 / (16.0 * (t8 - t16)), ov = 2.0 * t16 - t8;
+    if (rate > 0 && ov >= 0) {
+      m.group_rate = rate;
+      m.overhead_g = ov;
+      got_g = true;
+    }
+  }
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->model = m;
+  b->autotuned = got1 && got_g;
+}
+
 }  // namespace
 
 extern "C" {
@@ -696,6 +819,8 @@ void cg_batch_opts_default(cg_batch_opts* o) {
   o->group_override = 0;
   o->validate = 1;
   o->preconditioner = CG_PRECOND_NONE;
+  o->autotune = 0;
+  o->group_target_ms = 50;
 }
 
 const char* cg_batch_last_error(cg_batch b) {
@@ -716,7 +841,8 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
     return bfail(nullptr, CG_EINVAL, "cg_batch_create: unknown precision");
   if (o.max_systems <= 0 || o.max_systems > (1 << 20) || o.chunk_iters < 0 || o.replace_every < 0 ||
       o.budget_bytes < 0 || o.max_pending <= 0 || o.group_override < 0 ||
-      (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI))
+      (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI) || o.autotune < 0 ||
+      o.autotune > 1 || o.group_target_ms <= 0)
     return bfail(nullptr, CG_EINVAL, "cg_batch_create: bad option");
   auto b = std::make_unique<cg_batch_ctx>();
   if (o.device >= 0) b->device = o.device;
@@ -733,6 +859,7 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   b->wait_ns = static_cast<unsigned long long>(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
   b->max_pending = o.max_pending;
   b->group_override = o.group_override;
+  b->model.target_s = 1e-3 * o.group_target_ms;
   b->validate = o.validate != 0;
   b->use_graph = o.use_graph != 0;
   b->t0 = std::chrono::steady_clock::now();
@@ -795,6 +922,7 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail_cuda(e, "cg_batch_create: synchronize");
   cg_batch_ctx* raw = b.release();
   raw->worker = std::thread(worker_main, raw);
+  if (o.autotune) calibrate(raw);
   *out = raw;
   return CG_OK;
 }
@@ -901,6 +1029,12 @@ int cg_batch_get_stats(cg_batch b, cg_batch_stats* st) {
   st->nblocks = b->nblocks;
   st->round_ms_total = b->round_ms_total;
   st->last_round_ms = b->last_round_ms;
+  st->cta_bytes_per_s = b->model.cta_rate;
+  st->group_cta_bytes_per_s = b->model.group_rate;
+  st->step_overhead_s = b->model.overhead_1;
+  st->group_step_overhead_s = b->model.overhead_g;
+  st->autotuned = b->autotuned ? 1 : 0;
+  st->pad = 0;
   return CG_OK;
 }
 

@@ -280,3 +280,23 @@ def test_served_request_joins_running_rounds_with_the_same_bits():
     assert rl.admit_ms < max(r.done_ms for r in res[:-1])
     for (S, bs), req, r in zip(others, reqs, res[:-1]):
         _check_vs_oracle(S, bs, r, _x(req))
+
+
+def test_autotuned_group_model():
+    """The autotuner measures the group-size cost model on the GPU; the model
+    is positive and self-consistent, a large system gets a larger group than
+    a small one, and solves still match the oracle."""
+    cg = cg_mod()
+    with cg.Batch(autotune=True) as bt:
+        st = bt.stats()
+        assert st["autotuned"] == 1
+        assert st["cta_bytes_per_s"] > 1e9 and st["group_cta_bytes_per_s"] > 1e9
+        assert st["step_overhead_s"] >= 0 and st["group_step_overhead_s"] >= 0
+        g_small = bt.group_for(fi.q1(8, 1.0, 1).row_ptr)
+        g_big = bt.group_for(fi.q1(48, 1.0, 1).row_ptr)
+        assert 1 <= g_small <= g_big <= st["nblocks"]
+        systems = [_system(N, 1300 + N) for N in (6, 12)]
+        reqs = [_request(A, b) for A, b in systems]
+        res = _wait_all(bt, bt.submit(reqs))
+    for (A, b), req, r in zip(systems, reqs, res):
+        _check_vs_oracle(A, b, r, _x(req))
