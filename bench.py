@@ -76,6 +76,7 @@ def parse(argv=None):
     ap.add_argument("--group-target-ms", type=int, default=50, help="batch/serve: solo time a group aims at")
     ap.add_argument("--matrix", default="q1", choices=["q1", "lap7"],
                     help="q1: the Q1 FE system (default); lap7: the 7-point Laplacian (with --grid 16: n = 4096)")
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs of the persistent kernel (0: automatic)")
     ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
                     help="none: the paper's plain CG; jacobi: preconditioned by diag(A)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
@@ -434,7 +435,7 @@ def run_ours(args):
     mixed = args.precision == "mixed"
     jac = args.precond == "jacobi"
     h = cg.cg_create(rp, ci, va, stream=stream, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64,
-                     preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE)
+                     preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE, ctas=args.ctas)
     h64 = cg.cg_create(rp, ci, va, stream=stream) if mixed else None   # FP64 solve for the accuracy record
     del rp, ci, va
     xs_d = torch.from_numpy(xs).to(dev)
@@ -577,7 +578,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.grid, args.precision, args.precond, args.matrix),
                    "n": n, "nnz": nnz, "iters": iters, "tol": TOL, "x0": "zero",
-                   "l2": "flushed before every timed solve (256 MiB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed before every timed solve (256 MiB write)", "parallelism": f"replicas x{world}",
+                   "ctas": h.nblocks},
         "roofline": roof,
         "accuracy": accuracy,
         "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm_peak, "ms": spmv_ms, "bytes": spmv_bytes(n, nnz),

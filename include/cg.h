@@ -83,7 +83,9 @@ typedef struct {
   int32_t validate;       /* 1 (default): check the CSR in cg_create (O(n + nnz) on the host) */
   int32_t wait_limit_ms;  /* bound on any device-side wait inside a kernel (default 2000) */
   int32_t preconditioner; /* cg_preconditioner (default CG_PRECOND_NONE) */
-  int32_t reserved[6];    /* zero */
+  int32_t ctas;           /* CTAs of the persistent kernels (at most one per SM); 0 (default):
+                             one per SM */
+  int32_t reserved[5];    /* zero */
 } cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -36,7 +36,7 @@ class cg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("replace_every", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class cg_batch_opts(ctypes.Structure):
@@ -214,7 +214,7 @@ class Handle:
 def cg_create(row_ptr, col_idx, val, n: int | None = None, nnz: int | None = None, index_base: int = 0,
               stream=None, device: int | None = None, precision: int = CG_PREC_FP64,
               replace_every: int = 50, validate: bool = True, wait_limit_ms: int = 2000,
-              preconditioner: int = CG_PRECOND_NONE) -> Handle:
+              preconditioner: int = CG_PRECOND_NONE, ctas: int = 0) -> Handle:
     """cg_create: copy a CSR matrix (IA/JA/AA; host or CUDA arrays) to the GPU.
 
     ``stream``: a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int, or None for
@@ -251,6 +251,7 @@ def cg_create(row_ptr, col_idx, val, n: int | None = None, nnz: int | None = Non
     o.validate = 1 if validate else 0
     o.wait_limit_ms = int(wait_limit_ms)
     o.preconditioner = int(preconditioner)
+    o.ctas = int(ctas)
     out = ctypes.c_void_p(0)
     _check(lib.cg_create(ctypes.byref(out), ctypes.byref(csr), n, nnz, ctypes.byref(o)))
     return Handle(out.value, n, nnz, s)

@@ -223,6 +223,7 @@ void cg_opts_default(cg_opts* o) {
   o->validate = 1;
   o->wait_limit_ms = 2000;
   o->preconditioner = CG_PRECOND_NONE;
+  o->ctas = 0;
 }
 
 const char* cg_last_error(cg_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
@@ -244,6 +245,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   if (o.replace_every < 0) return fail(nullptr, CG_EINVAL, "cg_create: replace_every must be >= 0");
   if (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI)
     return fail(nullptr, CG_EINVAL, "cg_create: unknown preconditioner");
+  if (o.ctas < 0) return fail(nullptr, CG_EINVAL, "cg_create: ctas must be >= 0");
   if (!csr->row_ptr || (nnz > 0 && (!csr->col_idx || !csr->val)))
     return fail(nullptr, CG_EINVAL, "cg_create: NULL CSR array");
 
@@ -329,6 +331,10 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     return rc;
   }
   h->nblocks = sms * per_sm;
+  // every SM unless the caller asks for fewer: measured on GB300, fewer CTAs
+  // do not shorten the solve of small systems (a 16^3 7-point system takes
+  // 0.90 ms on 152 CTAs, 0.93 ms on 16 and 1.85 ms on one)
+  if (o.ctas > 0) h->nblocks = std::min(h->nblocks, o.ctas);
   if (h->nblocks > 1024) {  // the group-wide fixed-point sum takes at most 1024 CTA values
     int rc = fail(nullptr, CG_ECUDA, "cg_create: more persistent CTAs than the grid-wide sum supports");
     release(h);

@@ -1,0 +1,74 @@
+"""Solver paths that the finite-element systems do not reach, through the C
+ABI: the mixed-precision product on rows of two-lanes-per-row and whole-warp
+steps (rows of 33-64 and of more than 64 entries), and explicit CTA counts of
+the persistent kernel (one CTA: no group barrier at all; a few CTAs; the
+automatic choice)."""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+import oracle
+from gpu_util import cg_mod, handle, iters_close, kappa_estimate
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def _solve(h, b):
+    import torch
+    cg = cg_mod()
+    bd = torch.as_tensor(b, dtype=torch.float64).cuda()
+    xd = torch.zeros_like(bd)
+    res = cg.cg_solve(h, bd, xd, tol=TOL, maxit=20 * b.shape[0])
+    return res, xd.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,density", [(500, 0.09), (300, 0.3)])
+def test_mixed_precision_irregular_rows(n, density):
+    cg = cg_mod()
+    A = fi.random_spd(n, 50 + n, density=density, shift=0.05)
+    lens = np.diff(A.row_ptr)
+    assert lens.max() > 32  # the FP32 ring product's pair / long-row steps are used
+    b = oracle.spmv(A, fi.xstar(5, A.n))
+    with handle(A, precision=cg.CG_PREC_MIXED) as h:
+        res, x = _solve(h, b)
+    assert res.status == cg.CG_OK, (res, cg.last_error())
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= TOL * np.linalg.norm(b) * 1.0000001
+    ref = oracle.cg_mixed(A, b, tol=TOL, maxit=20 * A.n)
+    assert ref.status == oracle.OK
+    kap = kappa_estimate(A, b)
+    assert np.linalg.norm(x - ref.x) <= 2.02 * kap * TOL * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 17, 0])
+def test_cta_counts(ctas):
+    cg = cg_mod()
+    A = fi.q1(14, 1.0, 61)
+    b = oracle.spmv(A, fi.xstar(61, A.n))
+    with handle(A, ctas=ctas) as h:
+        if ctas:
+            assert h.nblocks == ctas
+        else:
+            assert 1 <= h.nblocks
+        res, x = _solve(h, b)
+    assert res.status == cg.CG_OK and res.relres <= TOL
+    ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
+    assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+
+
+def test_cta_count_products_agree_bitwise():
+    """The CSR product's bits do not depend on the CTA count (each row is
+    summed by one lane in storage order)."""
+    import torch
+    cg = cg_mod()
+    A = fi.q1(13, 1.0, 62)
+    x = torch.from_numpy(fi.xstar(62, A.n)).cuda()
+    ys = []
+    for c in (1, 5, 0):
+        with handle(A, ctas=c) as h:
+            y = torch.empty_like(x)
+            cg.cg_spmv(h, x, y)
+            ys.append(y.cpu().numpy())
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
