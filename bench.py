@@ -548,7 +548,9 @@ def run_ours(args):
     flops_launch = solve_flops(n, nnz, iters, mixed, jacobi=jac)
     achieved_gbs = bytes_launch / launch_s / 1e9
     achieved_gflops = flops_launch / launch_s / 1e9
-    kname = f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>"
+    side_x = n <= 8192 * h.nblocks  # the library's choice of kernel for small CTA shares
+    kname = (f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}, "
+             f"{'true' if side_x else 'false'}>")
     traffic = recorded_traffic(kname, f"{args.matrix}_{args.grid}")
     if l2_resident(n, nnz, mixed) or not mixed and achieved_gflops / FP64_PEAK_GFLOPS > achieved_gbs / hbm_peak:
         # the system stays in L2 during a solve (or the FP64 pipe is nearer its

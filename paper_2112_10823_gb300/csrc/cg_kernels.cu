@@ -31,7 +31,7 @@ namespace cgk {
 
 // One system on the whole grid: CTA c is rank c of the group.  kJacobi:
 // preconditioned by M = diag(A) (P.dinv).
-template <bool kMixed, bool kJacobi>
+template <bool kMixed, bool kJacobi, bool kSideX>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw};
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     solve_producer<kMixed>(sm, cs, P);
     return;
   }
-  solve_consumers<kMixed, kJacobi>(sm, cs, P, blockIdx.x);
+  solve_consumers<kMixed, kJacobi, kSideX>(sm, cs, P, blockIdx.x);
 }
 
 // y = A x (same partition and stream as the solve; one pass).
@@ -88,11 +88,16 @@ cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* er
 
 size_t spmv_smem_bytes() { return RingSmem::kBytes; }
 
-const void* solve_kernel_ptr(bool mixed, bool jacobi) {
-  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<true, true>)
-                           : reinterpret_cast<const void*>(cg_solve_kernel<true, false>);
-  return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<false, true>)
-                : reinterpret_cast<const void*>(cg_solve_kernel<false, false>);
+template <bool kSideX>
+const void* solve_kernel_ptr_t(bool mixed, bool jacobi) {
+  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<true, true, kSideX>)
+                           : reinterpret_cast<const void*>(cg_solve_kernel<true, false, kSideX>);
+  return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<false, true, kSideX>)
+                : reinterpret_cast<const void*>(cg_solve_kernel<false, false, kSideX>);
+}
+
+const void* solve_kernel_ptr(bool mixed, bool jacobi, bool side_x = false) {
+  return side_x ? solve_kernel_ptr_t<true>(mixed, jacobi) : solve_kernel_ptr_t<false>(mixed, jacobi);
 }
 
 int solve_blocks_per_sm(bool mixed, bool jacobi) {
@@ -105,7 +110,8 @@ int solve_blocks_per_sm(bool mixed, bool jacobi) {
 
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
   void* args[] = {const_cast<SolveParams*>(&P)};
-  const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr);
+  const bool side_x = P.A.n <= static_cast<int64_t>(kSideXRows) * P.A.nblocks;
+  const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr, side_x);
   cudaError_t e = ensure_smem_attr(k, RingSmem::kBytes);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(P.A.nblocks), dim3(kBlock), args, RingSmem::kBytes, s);

@@ -42,14 +42,21 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
   __syncwarp();
 }
 
+// Systems whose CTAs hold at most this many rows (small, L2-resident shares)
+// use the kernels that update x behind the barrier of the r.r sum, where the
+// wait is longer than the update; larger shares update x together with p
+// (one pass over p).  Both compute the same bits.
+constexpr int kSideXRows = 8192;
+
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
-// launch saved, for at most P.chunk_iters steps.
+// launch saved, for at most P.chunk_iters steps.  kSideX: x is updated by
+// warps 1.. behind the barrier of the r.r sum (see kSideXRows).
 //
 // Scalars live in the CTA state in shared memory (thread 0 updates them
 // between CTA barriers; every thread reads them after one), so that the
 // registers of the step loop's product are the product's own.
-template <bool kMixed, bool kJacobi>
+template <bool kMixed, bool kJacobi, bool kSideX>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
                                                 const int rank) {
   const DevCsr& A = P.A;
@@ -73,8 +80,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   // fin(sums), which updates the CTA state; one CTA barrier publishes it.
   // Two slots of partials (3 nb values each) alternate so that a fast CTA
   // publishing the next sum never overwrites values a slow CTA still reads.
+  // `side()` runs in warps 1.. while warp 0 does this: work of the step that
+  // needs no group-wide value yet, hidden behind the barrier.
   // Returns false in every thread if a wait gave up, here or anywhere before.
-  auto group_sum = [&](bool ok, int nv, double v0, double v1, double v2, auto&& fin) -> bool {
+  auto group_sum = [&](bool ok, int nv, double v0, double v1, double v2, auto&& fin, auto&& side) -> bool {
     const double vin[kMaxSumValues] = {v0, v1, v2};
     FxPart fp[kMaxSumValues];
 #pragma unroll
@@ -118,10 +127,13 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         st->ok = good ? 1 : 0;
         if (good) fin(sum);
       }
+    } else {
+      side();
     }
     cta_sync();
     return st->ok != 0;
   };
+  auto no_side = [] {};
   // Group barrier of all threads: every write before it is visible to every
   // CTA of the group after it.
   auto group_sync = [&]() -> bool {
@@ -183,7 +195,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           st->rr = sum[0];
           st->bnorm2 = sum[1];
           st->rho = kJacobi ? sum[2] : sum[0];
-        })) {
+        }, no_side)) {
       solve_fail(sm, P);
       return;
     }
@@ -236,7 +248,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           const double gamma = sum[0];
           if (!(gamma > 0.0) || !isfinite(gamma)) st->flags |= kFlagBreakdown;  // not SPD, or overflow
           else st->alpha = st->rho / gamma;
-        })) {
+        }, no_side)) {
       solve_fail(sm, P);
       return;
     }
@@ -267,6 +279,28 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         }
       }
     }
+    // kSideX: x += alpha p by warps 1.. while warp 0 does the sum below (x is
+    // needed again only by the next residual replacement or at the end)
+    auto side_x = [&] {
+      if constexpr (kSideX) {
+        for (int base = row0 + tid - 32; base < row1; base += 4 * (kConsumers - 32)) {
+          double pv[4], xv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = base + u * (kConsumers - 32);
+            if (i < row1) {
+              pv[u] = p[i];
+              xv[u] = x[i];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = base + u * (kConsumers - 32);
+            if (i < row1) x[i] = fma(alpha, pv[u], xv[u]);
+          }
+        }
+      }
+    };
     if (!group_sum(true, kJacobi ? 2 : 1, acc_r, acc_z, 0.0, [&](const double* sum) {
           const long long k = st->k + 1;
           st->k = k;
@@ -283,16 +317,17 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
             if (rr <= st->thresh2) st->flags |= kFlagDone;
             st->rho = rho_new;
           }
-        })) {
+        }, side_x)) {
       solve_fail(sm, P);
       return;
     }
     const int32_t f = st->flags;
     const double beta = st->beta;
     if (f & kFlagReplace) {
-      // x += alpha p, then r = b - A x in FP64 (residual replacement); r, rr
-      // and rho take the true residual's values
-      for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
+      // x += alpha p (unless done behind the sum), then r = b - A x in FP64
+      // (residual replacement); r, rr and rho take the true residual's values
+      if constexpr (!kSideX)
+        for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
       if (!group_sync()) { solve_fail(sm, P); return; }
       double acc_t = 0.0, acc_tz = 0.0;
       auto epi = [&](int i, double s, double bi) {
@@ -307,7 +342,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
             st->rho = kJacobi ? sum[1] : sum[0];
             st->flags &= ~kFlagReplace;
             if (sum[0] <= st->thresh2) st->flags |= kFlagDone;
-          })) {
+          }, no_side)) {
         solve_fail(sm, P);
         return;
       }
@@ -320,8 +355,32 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         if constexpr (kMixed) P.p32[i] = static_cast<float>(pi);
       }
     } else if (f & kFlagDone) {
-      for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
+      if constexpr (!kSideX)
+        for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
       break;
+    } else if constexpr (kSideX) {
+      // ---- p = z + beta p   (z = dinv .* r, or r; x was updated behind the sum)
+      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
+        double pv[4], zv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kConsumers;
+          if (i < row1) {
+            pv[u] = p[i];
+            zv[u] = r[i];
+            if constexpr (kJacobi) zv[u] = P.dinv[i] * zv[u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = base + u * kConsumers;
+          if (i < row1) {
+            const double pn = fma(beta, pv[u], zv[u]);
+            p[i] = pn;
+            if constexpr (kMixed) P.p32[i] = static_cast<float>(pn);
+          }
+        }
+      }
     } else {
       // ---- x += alpha p; p = z + beta p   (z = dinv .* r, or r)
       for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
@@ -385,7 +444,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           ctrl->relres_true = sqrt(sum[0] / st->bnorm2);
           ctrl->phase = kPhaseDone;
         }
-      })) {
+      }, no_side)) {
     solve_fail(sm, P);
     return;
   }
