@@ -513,6 +513,33 @@ def run_ours(args):
     joules = (e1 - e0) / args.latency_solves if (e0 is not None and e1 is not None) else None
     watts = (e1 - e0) / tl if (e0 is not None and e1 is not None) else None
 
+    # ---- BLAS-1 kernels alone (the vector operations of Sec. 5.2): the paper's
+    # largest vector length and one four times the L2 (L2 flushed before each
+    # call); bytes: dot 16 per element, axpy and element-wise product 24
+    blas1 = {}
+    for nv in (5_000_000, 64_000_000):
+        xv = torch.rand(nv, dtype=torch.float64, device=dev)
+        yv = torch.rand(nv, dtype=torch.float64, device=dev)
+        zv = torch.empty_like(xv)
+        outv = torch.zeros(1, dtype=torch.float64, device=dev)
+        ops = {"dot": (lambda: cg.cg_dot(h, xv, yv, outv), 16), "axpy": (lambda: cg.cg_axpy(h, 0.5, xv, yv), 24),
+               "ewmul": (lambda: cg.cg_ewmul(h, xv, yv, zv), 24)}
+        for name, (fn, bpe) in ops.items():
+            for _ in range(3):
+                fn()
+            tms = []
+            for k in range(10):
+                flush.fill_(k)
+                s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s_ev.record(stream)
+                fn()
+                e_ev.record(stream)
+                e_ev.synchronize()
+                tms.append(s_ev.elapsed_time(e_ev))
+            ms = float(np.median(tms))
+            blas1[f"{name}_{nv}"] = {"us": 1000 * ms, "gbs": bpe * nv / (ms * 1e-3) / 1e9}
+        del xv, yv, zv
+
     # ---- CSR product alone (L2 flushed before each call)
     yv = torch.empty_like(b)
     for _ in range(3):
@@ -586,6 +613,7 @@ def run_ours(args):
         "accuracy": accuracy,
         "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm_peak, "ms": spmv_ms, "bytes": spmv_bytes(n, nnz),
                  "l2": "flushed before every call", "precision": "fp64"},
+        "blas1": {k: dict(v, frac=v["gbs"] / hbm_peak) for k, v in blas1.items()},
         "energy": {"joules_per_solve": joules, "avg_watts": watts, "source": "NVML board energy",
                    "solves": args.latency_solves},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

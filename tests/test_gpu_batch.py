@@ -300,3 +300,19 @@ def test_autotuned_group_model():
         res = _wait_all(bt, bt.submit(reqs))
     for (A, b), req, r in zip(systems, reqs, res):
         _check_vs_oracle(A, b, r, _x(req))
+
+
+def test_destroy_with_work_in_flight():
+    """Destroying a batch object while requests are queued and running
+    returns after the round in flight; a new batch object then works."""
+    cg = cg_mod()
+    systems = [_system(N, 1400 + N) for N in (10, 14, 18, 22)]
+    bt = cg.Batch(chunk_iters=3, budget_bytes=64 << 20)
+    reqs = [_request(A, b) for A, b in systems * 3]
+    bt.submit(reqs)
+    bt.close()
+    A, b = systems[0]
+    with cg.Batch() as bt2:
+        r = _request(A, b)
+        res = _wait1(bt2, bt2.submit([r])[0])
+    _check_vs_oracle(A, b, res, _x(r))
