@@ -306,7 +306,9 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts);
 
 /* Stop the worker (after the round in flight), drop queued requests and
  * release everything.  Pointers of unfinished requests are never touched
- * again.  NULL is accepted. */
+ * again.  No other call on b may run concurrently with this one or follow
+ * it.  NULL is accepted.  The other cg_batch_* calls may be made from any
+ * number of host threads at once. */
 int cg_batch_destroy(cg_batch b);
 
 /*
