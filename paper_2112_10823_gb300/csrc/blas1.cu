@@ -6,10 +6,13 @@
 
 namespace cgk {
 
+// Threads per CTA of the vector kernels.
+constexpr int kVecBlock = 384;
+
 // Grid of the dot kernel: enough CTAs to fill the GPU for long vectors, no
 // more than needed for short ones.  Depends only on n and the SM count.
 int dot_grid(int64_t n, int num_sms) {
-  const int64_t per_cta = static_cast<int64_t>(kBlock) * 8;
+  const int64_t per_cta = static_cast<int64_t>(kVecBlock) * 8;
   int64_t g = (n + per_cta - 1) / per_cta;
   const int64_t cap = static_cast<int64_t>(num_sms) * 4;
   if (g > cap) g = cap;
@@ -21,13 +24,13 @@ int dot_grid(int64_t n, int num_sms) {
 // grid, four independent accumulators combined in a fixed order), the CTA sums
 // its threads, and the last CTA to finish adds the CTA partials in CTA order
 // and resets the arrival counter for the next call.
-__global__ void __launch_bounds__(kBlock) dot_kernel(int64_t n, const double* __restrict__ x,
+__global__ void __launch_bounds__(kVecBlock) dot_kernel(int64_t n, const double* __restrict__ x,
                                                      const double* __restrict__ y, double* __restrict__ out,
                                                      double* __restrict__ partials, unsigned int* counter) {
-  __shared__ double red[kBlock + 4];
+  __shared__ double red[kVecBlock + 4];
   __shared__ unsigned int is_last;
-  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
-  int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kVecBlock;
+  int64_t i = static_cast<int64_t>(blockIdx.x) * kVecBlock + threadIdx.x;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   for (; i + 3 * T < n; i += 4 * T) {
     a0 = fma(x[i], y[i], a0);
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t n, const double* __
   if (is_last) {
     __threadfence();
     double t = 0.0;
-    for (int j = threadIdx.x; j < static_cast<int>(gridDim.x); j += kBlock) t += __ldcg(partials + j);
+    for (int j = threadIdx.x; j < static_cast<int>(gridDim.x); j += kVecBlock) t += __ldcg(partials + j);
     t = block_sum(t, red);
     if (threadIdx.x == 0) {
       *out = t;
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t n, const double* __
 
 cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out, double* partials,
                        unsigned int* counter, int grid, cudaStream_t s) {
-  dot_kernel<<<grid, kBlock, 0, s>>>(n, x, y, out, partials, counter);
+  dot_kernel<<<grid, kVecBlock, 0, s>>>(n, x, y, out, partials, counter);
   return cudaGetLastError();
 }
 
@@ -66,7 +69,7 @@ namespace {
 inline int stream_grid(int64_t n) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (n / 2 + kBlock - 1) / kBlock;
+  const int64_t want = (n / 2 + kVecBlock - 1) / kVecBlock;
   const int64_t cap = static_cast<int64_t>(sms) * 8;
   int64_t g = want < cap ? want : cap;
   return g < 1 ? 1 : static_cast<int>(g);
@@ -77,10 +80,10 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 // y <- a x + y.  Pairs of elements move as 16-byte loads/stores when both
 // vectors are 16-byte aligned; otherwise element by element.
 template <bool kVec>
-__global__ void __launch_bounds__(kBlock) axpy_kernel(int64_t n, double a, const double* __restrict__ x,
+__global__ void __launch_bounds__(kVecBlock) axpy_kernel(int64_t n, double a, const double* __restrict__ x,
                                                       double* __restrict__ y) {
-  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
-  int64_t t = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kVecBlock;
+  int64_t t = static_cast<int64_t>(blockIdx.x) * kVecBlock + threadIdx.x;
   if constexpr (kVec) {
     const int64_t n2 = n / 2;
     const double2* x2 = reinterpret_cast<const double2*>(x);
@@ -99,10 +102,10 @@ __global__ void __launch_bounds__(kBlock) axpy_kernel(int64_t n, double a, const
 }
 
 template <bool kVec>
-__global__ void __launch_bounds__(kBlock) ewmul_kernel(int64_t n, const double* x, const double* y,
+__global__ void __launch_bounds__(kVecBlock) ewmul_kernel(int64_t n, const double* x, const double* y,
                                                        double* z) {  // z may alias x or y
-  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
-  int64_t t = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kVecBlock;
+  int64_t t = static_cast<int64_t>(blockIdx.x) * kVecBlock + threadIdx.x;
   if constexpr (kVec) {
     const int64_t n2 = n / 2;
     const double2* x2 = reinterpret_cast<const double2*>(x);
@@ -120,15 +123,15 @@ __global__ void __launch_bounds__(kBlock) ewmul_kernel(int64_t n, const double* 
 
 cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
   const int g = stream_grid(n);
-  if (aligned16(x) && aligned16(y)) axpy_kernel<true><<<g, kBlock, 0, s>>>(n, a, x, y);
-  else axpy_kernel<false><<<g, kBlock, 0, s>>>(n, a, x, y);
+  if (aligned16(x) && aligned16(y)) axpy_kernel<true><<<g, kVecBlock, 0, s>>>(n, a, x, y);
+  else axpy_kernel<false><<<g, kVecBlock, 0, s>>>(n, a, x, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ewmul(int64_t n, const double* x, const double* y, double* z, cudaStream_t s) {
   const int g = stream_grid(n);
-  if (aligned16(x) && aligned16(y) && aligned16(z)) ewmul_kernel<true><<<g, kBlock, 0, s>>>(n, x, y, z);
-  else ewmul_kernel<false><<<g, kBlock, 0, s>>>(n, x, y, z);
+  if (aligned16(x) && aligned16(y) && aligned16(z)) ewmul_kernel<true><<<g, kVecBlock, 0, s>>>(n, x, y, z);
+  else ewmul_kernel<false><<<g, kVecBlock, 0, s>>>(n, x, y, z);
   return cudaGetLastError();
 }
 
@@ -138,13 +141,13 @@ namespace cgk {
 
 // FP32 copy of the matrix values (mixed-precision handles), round to nearest.
 __global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
-  const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < n; i += T)
+  const int64_t T = static_cast<int64_t>(gridDim.x) * kVecBlock;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * kVecBlock + threadIdx.x; i < n; i += T)
     dst[i] = __double2float_rn(src[i]);
 }
 
 cudaError_t launch_f64_to_f32(int64_t n, const double* src, float* dst, cudaStream_t s) {
-  f64_to_f32_kernel<<<stream_grid(n), kBlock, 0, s>>>(n, src, dst);
+  f64_to_f32_kernel<<<stream_grid(n), kVecBlock, 0, s>>>(n, src, dst);
   return cudaGetLastError();
 }
 
@@ -208,7 +211,7 @@ cudaError_t launch_dot_noalloc(int64_t n, const double* x, const double* y, doub
   if (e != cudaSuccess) return e;
   int64_t grid = (n + kNoAllocElemsPerCta - 1) / kNoAllocElemsPerCta;
   if (grid < 1) grid = 1;
-  dot_kernel<<<static_cast<unsigned int>(grid), kBlock, 0, s>>>(n, x, y, out, scratch, counter);
+  dot_kernel<<<static_cast<unsigned int>(grid), kVecBlock, 0, s>>>(n, x, y, out, scratch, counter);
   return cudaGetLastError();
 }
 

@@ -551,8 +551,7 @@ __device__ __forceinline__ void seg_gather_n(const int32_t* cp, int len, const X
 
 // Multiply-adds of a gathered segment, in storage order, with FMA.
 template <typename T, typename X, typename Acc, int N, int U>
-__device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U]) {
-  Acc s = Acc(0);
+__device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U], Acc s) {
 #pragma unroll
   for (int u = 0; u < N; ++u)
     if (u < len) s = fma(Acc(vp[u]), Acc(xv[u]), s);
@@ -563,25 +562,45 @@ __device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U])
 #define CGK_SEG_CASES(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) \
   M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
 
+#define CGK_SEG_CASES16(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+
 template <typename X, int U>
 __device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
-  static_assert(U == 32, "dispatch covers 1..32");
-  switch (wmax) {
+  static_assert(U == 32 || U == 16, "dispatch covers 1..U");
+  if constexpr (U == 32) {
+    switch (wmax) {
 #define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
-    CGK_SEG_CASES(CGK_G)
+      CGK_SEG_CASES(CGK_G)
 #undef CGK_G
-    default: break;
+      default: break;
+    }
+  } else {
+    switch (wmax) {
+#define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
+      CGK_SEG_CASES16(CGK_G)
+#undef CGK_G
+      default: break;
+    }
   }
 }
 
 template <typename T, typename X, typename Acc, int U>
-__device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U]) {
-  static_assert(U == 32, "dispatch covers 1..32");
-  switch (wmax) {
-#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv);
-    CGK_SEG_CASES(CGK_F)
+__device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U], Acc s) {
+  static_assert(U == 32 || U == 16, "dispatch covers 1..U");
+  if constexpr (U == 32) {
+    switch (wmax) {
+#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv, s);
+      CGK_SEG_CASES(CGK_F)
 #undef CGK_F
-    default: return Acc(0);
+      default: return s;
+    }
+  } else {
+    switch (wmax) {
+#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv, s);
+      CGK_SEG_CASES16(CGK_F)
+#undef CGK_F
+      default: return s;
+    }
   }
 }
 
@@ -734,9 +753,22 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
       Acc part;
       if constexpr (kRingPass) {
         const int wmax = (m0 >> kWmaxShift) & 0xff;
-        X xv[kLaneMax];
-        seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
-        part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv);
+        if constexpr (sizeof(X) == 8) {
+          // FP64 gathers in batches of 16 (the same FMAs in the same order;
+          // half the registers held by gathered values)
+          X xv[16];
+          const int w0 = wmax < 16 ? wmax : 16;
+          seg_gather<X, 16>(rc + p0, len, w0, x, xv);
+          part = seg_fma<T, X, Acc, 16>(rv + p0, len, w0, xv, Acc(0));
+          if (wmax > 16) {
+            seg_gather<X, 16>(rc + p0 + 16, len - 16, wmax - 16, x, xv);
+            part = seg_fma<T, X, Acc, 16>(rv + p0 + 16, len - 16, wmax - 16, xv, part);
+          }
+        } else {
+          X xv[kLaneMax];
+          seg_gather<X, kLaneMax>(rc + p0, len, wmax, x, xv);
+          part = seg_fma<T, X, Acc, kLaneMax>(rv + p0, len, wmax, xv, Acc(0));
+        }
       } else {
         // the direct pass (rare: residual replacements) uses the compact
         // loop: the same FMAs in the same order, far fewer registers

@@ -9,8 +9,8 @@ namespace cgk {
 // The persistent kernels run one CTA per SM: kConsumerWarps consumer warps
 // that compute, plus one producer warp that streams the CSR matrix into a
 // shared-memory ring with 1-D TMA bulk copies (warp specialisation).
-constexpr int kConsumerWarps = 11;  // with the producer: three warps per SM sub-partition
-constexpr int kConsumers = kConsumerWarps * 32;  // 352 computing threads
+constexpr int kConsumerWarps = 15;  // with the producer: four warps per SM sub-partition
+constexpr int kConsumers = kConsumerWarps * 32;  // 480 computing threads
 constexpr int kBlock = kConsumers + 32;          // + the producer warp
 constexpr int kCtasPerSm = 1;
 constexpr int kWarps = kConsumerWarps;           // warps taking part in CTA reductions

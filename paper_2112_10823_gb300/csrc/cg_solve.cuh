@@ -48,6 +48,15 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
 // (one pass over p).  Both compute the same bits.
 constexpr int kSideXRows = 8192;
 
+// Rows per thread in flight in the vector phases (all loads of a batch
+// issued before any is used): as many as the registers that the product
+// leaves allow without spilling (128 per thread at 16 warps per CTA; the
+// Jacobi variants carry dinv as well, the fused x and p update three vectors).
+template <bool kJacobi, bool kSideX>
+__host__ __device__ constexpr int vec_rows() {
+  return kSideX ? (kJacobi ? 3 : 4) : (kJacobi ? 2 : 3);
+}
+
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
 // launch saved, for at most P.chunk_iters steps.  kSideX: x is updated by
@@ -70,6 +79,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   double* __restrict__ r = P.r;
   double* __restrict__ p = P.p;
   ConsumerCursor cur;
+  constexpr int kVR = vec_rows<kJacobi, kSideX>();
 
   // Group-wide sum of nv values per thread (nv <= 3), fused with the vote of
   // the consumer warps (`ok`: this thread's waits all succeeded).  Each warp
@@ -255,12 +265,12 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     if (st->flags & kFlagBreakdown) break;
     const double alpha = st->alpha;
 
-    // ---- r -= alpha q; rr = r.r and (Jacobi) r.z   (four rows per thread in flight)
+    // ---- r -= alpha q; rr = r.r and (Jacobi) r.z   (kVR rows per thread in flight)
     double acc_r = 0.0, acc_z = 0.0;
-    for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-      double qv[4], rv[4], dv[4];
+    for (int base = row0 + tid; base < row1; base += kVR * kConsumers) {
+      double qv[kVR], rv[kVR], dv[kVR];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kVR; ++u) {
         const int i = base + u * kConsumers;
         if (i < row1) {
           qv[u] = P.q[i];
@@ -269,7 +279,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kVR; ++u) {
         const int i = base + u * kConsumers;
         if (i < row1) {
           const double rn = fma(-alpha, qv[u], rv[u]);
@@ -283,10 +293,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     // needed again only by the next residual replacement or at the end)
     auto side_x = [&] {
       if constexpr (kSideX) {
-        for (int base = row0 + tid - 32; base < row1; base += 4 * (kConsumers - 32)) {
-          double pv[4], xv[4];
+        for (int base = row0 + tid - 32; base < row1; base += 2 * (kConsumers - 32)) {
+          double pv[2], xv[2];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 2; ++u) {
             const int i = base + u * (kConsumers - 32);
             if (i < row1) {
               pv[u] = p[i];
@@ -294,7 +304,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
             }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 2; ++u) {
             const int i = base + u * (kConsumers - 32);
             if (i < row1) x[i] = fma(alpha, pv[u], xv[u]);
           }
@@ -360,10 +370,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       break;
     } else if constexpr (kSideX) {
       // ---- p = z + beta p   (z = dinv .* r, or r; x was updated behind the sum)
-      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-        double pv[4], zv[4];
+      for (int base = row0 + tid; base < row1; base += kVR * kConsumers) {
+        double pv[kVR], zv[kVR];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kVR; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
             pv[u] = p[i];
@@ -372,7 +382,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kVR; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
             const double pn = fma(beta, pv[u], zv[u]);
@@ -383,10 +393,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       }
     } else {
       // ---- x += alpha p; p = z + beta p   (z = dinv .* r, or r)
-      for (int base = row0 + tid; base < row1; base += 4 * kConsumers) {
-        double pv[4], zv[4], xv[4];
+      for (int base = row0 + tid; base < row1; base += kVR * kConsumers) {
+        double pv[kVR], zv[kVR], xv[kVR];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kVR; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
             pv[u] = p[i];
@@ -396,7 +406,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kVR; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
             x[i] = fma(alpha, pv[u], xv[u]);
