@@ -2,9 +2,6 @@
 // Each CTA takes tasks (a system and its rank in the system's group of CTAs)
 // from a queue; the CG arithmetic of every task is the single-system solve's
 // (cg_solve.cuh).
-#include <mutex>
-#include <set>
-#include <utility>
 #include "cg_solve.cuh"
 
 namespace cgk {
@@ -18,7 +15,7 @@ namespace cgk {
 template <bool kMixed, bool kJacobi>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const RingSmem sm{smem_raw};
+  const RingSmem sm{smem_raw, kMixed ? 4u : 8u};  // FP32 values in the mixed solve's stream
   __shared__ int32_t task_id;
   bool reinit = false;
   for (;;) {
@@ -37,21 +34,6 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __gr
   }
 }
 
-namespace {
-cudaError_t batch_smem_attr(const void* kernel, size_t bytes) {
-  static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(mu);
-  if (done.count({kernel, dev})) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-  if (e == cudaSuccess) done.insert({kernel, dev});
-  return e;
-}
-}  // namespace
-
 const void* batch_kernel_ptr(bool mixed, bool jacobi) {
   if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_batch_kernel<true, true>)
                            : reinterpret_cast<const void*>(cg_batch_kernel<true, false>);
@@ -62,8 +44,9 @@ const void* batch_kernel_ptr(bool mixed, bool jacobi) {
 int batch_blocks_per_sm(bool mixed, bool jacobi) {
   int nb = 0;
   const void* k = batch_kernel_ptr(mixed, jacobi);
-  cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, RingSmem::kBytes);
+  const size_t smem = solve_smem_bytes(mixed);
+  cudaError_t e = ensure_smem_attr(k, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem);
   return e == cudaSuccess ? nb : -1;
 }
 
@@ -72,12 +55,13 @@ int batch_blocks_per_sm(bool mixed, bool jacobi) {
 // CUDA graph.
 cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblocks, cudaStream_t s) {
   const void* k = batch_kernel_ptr(mixed, jacobi);
-  cudaError_t e = batch_smem_attr(k, RingSmem::kBytes);
+  const size_t smem = solve_smem_bytes(mixed);
+  cudaError_t e = ensure_smem_attr(k, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblocks);
   cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = RingSmem::kBytes;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -403,30 +403,43 @@ struct SumScratch {
   int32_t ok[kWarps];
 };
 
+// Dynamic shared memory of a persistent CTA: the value ring (values of vb
+// bytes: 8 for FP64, 4 for FP32, so that an FP32 stream leaves the rest of
+// the SM's 256 KB to L1 for the gathers), the column ring, the slots'
+// mbarriers, the CTA state of a solve, the warp partials of its sums.
 struct RingSmem {
   static constexpr int kRingAlloc = kRing + kMirror;
-  static constexpr size_t kValBytes = sizeof(double) * kRingAlloc;
   static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc;
-  static constexpr size_t kBarOff = (kValBytes + kColBytes + 15) & ~size_t(15);
-  static constexpr size_t kStateOff = kBarOff + 16 * kSlots;
   static constexpr size_t kStateBytes = (sizeof(CtaState) + 15) & ~size_t(15);
-  static constexpr size_t kSumOff = kStateOff + kStateBytes;
   static constexpr size_t kSumBytes = (sizeof(SumScratch) + 15) & ~size_t(15);
-  static constexpr size_t kMiscOff = kSumOff + kSumBytes;
-  static constexpr size_t kBytes = kMiscOff + 64;
+  __host__ __device__ static constexpr size_t bar_off(size_t vb) {
+    return (vb * kRingAlloc + kColBytes + 15) & ~size_t(15);
+  }
+  __host__ __device__ static constexpr size_t state_off(size_t vb) { return bar_off(vb) + 16 * kSlots; }
+  __host__ __device__ static constexpr size_t sum_off(size_t vb) { return state_off(vb) + kStateBytes; }
+  __host__ __device__ static constexpr size_t misc_off(size_t vb) { return sum_off(vb) + kSumBytes; }
+  // Bytes of the whole layout for ring values of vb bytes.
+  __host__ __device__ static constexpr size_t bytes(size_t vb) { return misc_off(vb) + 64; }
 
   unsigned char* base;
+  uint32_t vb = sizeof(double);  // bytes per value in the ring
   template <typename T>
   __device__ T* val() const { return reinterpret_cast<T*>(base); }
-  __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + kValBytes); }
-  __device__ uint64_t* full(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + s; }
-  __device__ uint64_t* empty(int s) const { return reinterpret_cast<uint64_t*>(base + kBarOff) + kSlots + s; }
-  __device__ CtaState* state() const { return reinterpret_cast<CtaState*>(base + kStateOff); }
-  __device__ SumScratch* sums() const { return reinterpret_cast<SumScratch*>(base + kSumOff); }
-  __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + kMiscOff); }
-  __device__ int32_t* stop() const { return reinterpret_cast<int32_t*>(base + kMiscOff + 4); }
-  __device__ double* scalars() const { return reinterpret_cast<double*>(base + kMiscOff + 16); }
+  __device__ int32_t* col() const { return reinterpret_cast<int32_t*>(base + static_cast<size_t>(vb) * kRingAlloc); }
+  __device__ uint64_t* full(int s) const { return reinterpret_cast<uint64_t*>(base + bar_off(vb)) + s; }
+  __device__ uint64_t* empty(int s) const { return reinterpret_cast<uint64_t*>(base + bar_off(vb)) + kSlots + s; }
+  __device__ CtaState* state() const { return reinterpret_cast<CtaState*>(base + state_off(vb)); }
+  __device__ SumScratch* sums() const { return reinterpret_cast<SumScratch*>(base + sum_off(vb)); }
+  __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + misc_off(vb)); }
+  __device__ int32_t* stop() const { return reinterpret_cast<int32_t*>(base + misc_off(vb) + 4); }
+  __device__ double* scalars() const { return reinterpret_cast<double*>(base + misc_off(vb) + 16); }
 };
+
+// Ring layout of the kernels whose step-loop product streams values of type T.
+template <typename T>
+constexpr size_t ring_smem_bytes() {
+  return RingSmem::bytes(sizeof(T));
+}
 
 // The CTA's part of the matrix stream (identical in every thread).  Pieces
 // are numbered globally across passes (piece j of pass k is k * npieces + j);

@@ -146,7 +146,10 @@ cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblo
 int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
-// Shared-memory bytes of the streamed product (ring + scratch).
-size_t spmv_smem_bytes();
+// Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed).
+size_t solve_smem_bytes(bool mixed);
+// Opt a kernel in to `bytes` of dynamic shared memory with the smallest
+// carveout that holds them (once per kernel and device).
+cudaError_t ensure_smem_attr(const void* kernel, size_t bytes);
 
 }  // namespace cgk

@@ -34,7 +34,7 @@ namespace cgk {
 template <bool kMixed, bool kJacobi, bool kSideX>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const RingSmem sm{smem_raw};
+  const RingSmem sm{smem_raw, kMixed ? 4u : 8u};  // the step loop streams FP32 values in the mixed solve
   CtaStream cs;
   stream_setup(sm, cs, P.A, blockIdx.x);  // the last barrier of all threads
   if (threadIdx.x >= kConsumers) {
@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A
   consumers_done(sm);
 }
 
-namespace {
-// Opt a kernel in to the large dynamic shared memory, once per (kernel, device).
+// Opt a kernel in to `bytes` of dynamic shared memory, and ask for the
+// smallest shared-memory carveout that holds them (the rest of the SM's
+// 256 KB serves as L1 for the product's gathers), once per (kernel, device).
 cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
   static std::mutex mu;
   static std::set<std::pair<const void*, int>> done;
@@ -74,19 +75,26 @@ cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
   std::lock_guard<std::mutex> lock(mu);
   if (done.count({kernel, dev})) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  int max_sm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess && max_sm > 0) {
+    // a hint: the driver rounds it up to a configuration the launch fits in
+    const size_t need = bytes + 1024;  // + the CTA's reserved shared memory
+    int pct = static_cast<int>((need * 100 + static_cast<size_t>(max_sm) - 1) / static_cast<size_t>(max_sm));
+    if (pct > 100) pct = 100;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  }
   if (e == cudaSuccess) done.insert({kernel, dev});
   return e;
 }
-}  // namespace
 
 cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* err, cudaStream_t s) {
-  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(spmv_kernel), RingSmem::kBytes);
+  constexpr size_t kSmem = ring_smem_bytes<double>();
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(spmv_kernel), kSmem);
   if (e != cudaSuccess) return e;
-  spmv_kernel<<<A.nblocks, kBlock, RingSmem::kBytes, s>>>(A, x, y, err);
+  spmv_kernel<<<A.nblocks, kBlock, kSmem, s>>>(A, x, y, err);
   return cudaGetLastError();
 }
-
-size_t spmv_smem_bytes() { return RingSmem::kBytes; }
 
 template <bool kSideX>
 const void* solve_kernel_ptr_t(bool mixed, bool jacobi) {
@@ -100,21 +108,29 @@ const void* solve_kernel_ptr(bool mixed, bool jacobi, bool side_x = false) {
   return side_x ? solve_kernel_ptr_t<true>(mixed, jacobi) : solve_kernel_ptr_t<false>(mixed, jacobi);
 }
 
+size_t solve_smem_bytes(bool mixed) { return mixed ? ring_smem_bytes<float>() : ring_smem_bytes<double>(); }
+
 int solve_blocks_per_sm(bool mixed, bool jacobi) {
   int nb = 0;
-  const void* k = solve_kernel_ptr(mixed, jacobi);
-  cudaError_t e = ensure_smem_attr(k, RingSmem::kBytes);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, RingSmem::kBytes);
-  return e == cudaSuccess ? nb : -1;
+  const size_t smem = solve_smem_bytes(mixed);
+  // both variants (x behind the r.r sum or not) have the same resources
+  for (const bool side_x : {false, true}) {
+    const void* k = solve_kernel_ptr(mixed, jacobi, side_x);
+    cudaError_t e = ensure_smem_attr(k, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem);
+    if (e != cudaSuccess) return -1;
+  }
+  return nb;
 }
 
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
   void* args[] = {const_cast<SolveParams*>(&P)};
   const bool side_x = P.A.n <= static_cast<int64_t>(kSideXRows) * P.A.nblocks;
   const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr, side_x);
-  cudaError_t e = ensure_smem_attr(k, RingSmem::kBytes);
+  const size_t smem = solve_smem_bytes(mixed);
+  cudaError_t e = ensure_smem_attr(k, smem);
   if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel(k, dim3(P.A.nblocks), dim3(kBlock), args, RingSmem::kBytes, s);
+  return cudaLaunchCooperativeKernel(k, dim3(P.A.nblocks), dim3(kBlock), args, smem, s);
 }
 
 // dinv[i] = 1 / diag(A)_i (the diagonal summed over row i's entries in
