@@ -575,7 +575,7 @@ def run_ours(args):
     flops_launch = solve_flops(n, nnz, iters, mixed, jacobi=jac)
     achieved_gbs = bytes_launch / launch_s / 1e9
     achieved_gflops = flops_launch / launch_s / 1e9
-    side_x = n <= 8192 * h.nblocks  # the library's choice of kernel for small CTA shares
+    side_x = h.partition_info()[1]  # the library's kernel for small CTA shares
     kname = (f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}, "
              f"{'true' if side_x else 'false'}>")
     traffic = recorded_traffic(kname, f"{args.matrix}_{args.grid}")

@@ -116,6 +116,16 @@ const char* cg_last_error(cg_handle h);
 int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks);
 
 /*
+ * The row partition of the persistent kernels: *max_rows = the most rows
+ * in one CTA's range; *small_share = 1 if cg_solve runs the small-share
+ * kernel on this handle (every range at most 2560 rows: the range's
+ * residual kept in shared memory, x updated behind the r.r barrier; the
+ * same bits as the other kernel), else 0.  Either pointer may be NULL.
+ * Host only: no GPU work.
+ */
+int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* small_share);
+
+/*
  * y = A x (Sec. 2.3 / 5.2): y_i = sum_{k=IA(i)}^{IA(i+1)-1} AA(k) x(JA(k)),
  * FP64 with FMA, each row summed in storage order.  x, y: device pointers to
  * n doubles; x and y must not overlap.  Asynchronous on the handle's stream.

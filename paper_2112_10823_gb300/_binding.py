@@ -89,6 +89,8 @@ def _load() -> ctypes.CDLL:
     lib.cg_last_error.argtypes = [vp]
     lib.cg_info.restype = ctypes.c_int
     lib.cg_info.argtypes = [vp, P(i64), P(i64), P(i32)]
+    lib.cg_partition_info.restype = ctypes.c_int
+    lib.cg_partition_info.argtypes = [vp, P(i32), P(i32)]
     lib.cg_spmv.restype = ctypes.c_int
     lib.cg_spmv.argtypes = [vp, vp, vp]
     lib.cg_dot.restype = ctypes.c_int
@@ -191,6 +193,12 @@ class Handle:
         nb = ctypes.c_int32(0)
         _check(lib.cg_info(self._h, None, None, ctypes.byref(nb)), self._h)
         return nb.value
+
+    def partition_info(self):
+        """(most rows in one CTA's range, whether cg_solve runs the small-share kernel)."""
+        mr, ss = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib.cg_partition_info(self._h, ctypes.byref(mr), ctypes.byref(ss)), self._h)
+        return mr.value, bool(ss.value)
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -451,6 +451,8 @@ void admit(cg_batch_ctx* b) {
     P.A.n = static_cast<int32_t>(n);
     P.A.nsteps = static_cast<int32_t>(part.step.size()) - 2;
     P.A.nblocks = group;
+    for (int g = 0; g < group; ++g)
+      P.A.max_rows = std::max(P.A.max_rows, part.block_row[g + 1] - part.block_row[g]);
     P.A.nnz = nnz;
     P.b = reinterpret_cast<double*>(at(L.b));
     P.x = reinterpret_cast<double*>(at(L.x));

@@ -107,6 +107,7 @@ struct cg_ctx {
   int num_sms = 0;
   int nblocks = 0;
   int nsteps = 0;
+  int max_rows = 0;  // most rows in one CTA's range
   // device memory owned by the handle
   int32_t* d_row_ptr = nullptr;
   int32_t* d_col = nullptr;
@@ -193,6 +194,7 @@ cgk::DevCsr dev_view(const cg_ctx* h) {
   A.n = static_cast<int32_t>(h->n);
   A.nsteps = h->nsteps;
   A.nblocks = h->nblocks;
+  A.max_rows = h->max_rows;
   A.nnz = h->nnz;
   return A;
 }
@@ -345,6 +347,8 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   Partition part;
   build_partition(rp, n, h->nblocks, part);
   h->nsteps = static_cast<int>(part.step.size()) - 2;
+  for (int b = 0; b < h->nblocks; ++b)
+    h->max_rows = std::max(h->max_rows, part.block_row[b + 1] - part.block_row[b]);
 
   const size_t pad = cgk::kPadEntries;
   CG_TRY(dalloc(h, &h->d_row_ptr, n + 1), "cg_create: cudaMalloc");
@@ -432,6 +436,13 @@ int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks) {
   if (n) *n = h->n;
   if (nnz) *nnz = h->nnz;
   if (nblocks) *nblocks = h->nblocks;
+  return CG_OK;
+}
+
+int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* small_share) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_partition_info: NULL handle");
+  if (max_rows) *max_rows = h->max_rows;
+  if (small_share) *small_share = cgk::small_share(dev_view(h), 0) ? 1 : 0;
   return CG_OK;
 }
 

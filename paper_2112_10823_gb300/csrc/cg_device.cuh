@@ -433,12 +433,16 @@ struct RingSmem {
   __device__ int32_t* flag() const { return reinterpret_cast<int32_t*>(base + misc_off(vb)); }
   __device__ int32_t* stop() const { return reinterpret_cast<int32_t*>(base + misc_off(vb) + 4); }
   __device__ double* scalars() const { return reinterpret_cast<double*>(base + misc_off(vb) + 16); }
+  // r of the CTA's rows in a small-share solve, behind the layout
+  // (kLocalRows entries).
+  __device__ double* local() const { return reinterpret_cast<double*>(base + bytes(vb)); }
 };
 
-// Ring layout of the kernels whose step-loop product streams values of type T.
+// Dynamic shared memory of the kernels whose step-loop product streams
+// values of type T; `local`: with the small-share solve's r.
 template <typename T>
-constexpr size_t ring_smem_bytes() {
-  return RingSmem::bytes(sizeof(T));
+constexpr size_t ring_smem_bytes(bool local = false) {
+  return RingSmem::bytes(sizeof(T)) + (local ? sizeof(double) * kLocalRows : 0);
 }
 
 // The CTA's part of the matrix stream (identical in every thread).  Pieces

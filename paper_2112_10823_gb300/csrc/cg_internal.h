@@ -36,6 +36,11 @@ constexpr int kMirror = 32;
 // longer than the ring.  Steps of a CTA go to its consumer warps round-robin.
 constexpr int kStepNnz = 1024;
 constexpr int kLaneMax = 32;  // longest row computed by a single lane
+// Largest CTA share (rows) of the small-share solve kernels, which keep the
+// share's r in shared memory (20 KB behind the ring layout; the FP64 layout
+// then takes 218 KB of the 227 KB a CTA may have).
+constexpr int kLocalRows = 2560;
+
 // Padding (in entries) behind val/col allocations so that rounding a copy's
 // end up to 16 bytes never reads past the allocation.
 constexpr int kPadEntries = 8;
@@ -62,8 +67,15 @@ struct DevCsr {
   int32_t n;
   int32_t nsteps;
   int32_t nblocks;            // CTAs the partition was balanced for
+  int32_t max_rows;           // most rows in one CTA's range (host side; 0 if unknown)
   int64_t nnz;
 };
+
+// Whether a solve of A in one launch (chunk_iters <= 0) runs the small-share
+// kernel: every CTA's range fits kLocalRows.
+inline bool small_share(const DevCsr& A, int64_t chunk_iters) {
+  return A.max_rows > 0 && A.max_rows <= kLocalRows && chunk_iters <= 0;
+}
 
 // Control block of one solve, in device memory, cleared before its first
 // launch.  A solve may run over several launches (batched solves advance
@@ -146,8 +158,9 @@ cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblo
 int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
-// Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed).
-size_t solve_smem_bytes(bool mixed);
+// Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed;
+// `local`: the small-share kernels, with r of the share).
+size_t solve_smem_bytes(bool mixed, bool local = false);
 // Opt a kernel in to `bytes` of dynamic shared memory with the smallest
 // carveout that holds them (once per kernel and device).
 cudaError_t ensure_smem_attr(const void* kernel, size_t bytes);

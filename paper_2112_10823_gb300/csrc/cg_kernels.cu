@@ -21,6 +21,7 @@
 // shadow of p: the product is FP32 (FP32 accumulation); sums, alpha, beta, x
 // and r stay FP64; every `replace_every` steps, and before accepting
 // convergence, r is replaced by the FP64 true residual b - A x.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <set>
@@ -108,26 +109,31 @@ const void* solve_kernel_ptr(bool mixed, bool jacobi, bool side_x = false) {
   return side_x ? solve_kernel_ptr_t<true>(mixed, jacobi) : solve_kernel_ptr_t<false>(mixed, jacobi);
 }
 
-size_t solve_smem_bytes(bool mixed) { return mixed ? ring_smem_bytes<float>() : ring_smem_bytes<double>(); }
+size_t solve_smem_bytes(bool mixed, bool local) {
+  return mixed ? ring_smem_bytes<float>(local) : ring_smem_bytes<double>(local);
+}
 
 int solve_blocks_per_sm(bool mixed, bool jacobi) {
   int nb = 0;
-  const size_t smem = solve_smem_bytes(mixed);
-  // both variants (x behind the r.r sum or not) have the same resources
-  for (const bool side_x : {false, true}) {
-    const void* k = solve_kernel_ptr(mixed, jacobi, side_x);
+  for (const bool small : {false, true}) {  // both must fit (one CTA per SM)
+    const void* k = solve_kernel_ptr(mixed, jacobi, small);
+    const size_t smem = solve_smem_bytes(mixed, small);
     cudaError_t e = ensure_smem_attr(k, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem);
+    int nk = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nk, k, kBlock, smem);
     if (e != cudaSuccess) return -1;
+    nb = small ? std::min(nb, nk) : nk;
   }
   return nb;
 }
 
 cudaError_t launch_solve(const SolveParams& P, bool mixed, cudaStream_t s) {
   void* args[] = {const_cast<SolveParams*>(&P)};
-  const bool side_x = P.A.n <= static_cast<int64_t>(kSideXRows) * P.A.nblocks;
-  const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr, side_x);
-  const size_t smem = solve_smem_bytes(mixed);
+  // the small-share kernel: every CTA's rows fit its shared r, and the
+  // solve runs in this one launch
+  const bool small = small_share(P.A, P.chunk_iters);
+  const void* k = solve_kernel_ptr(mixed, P.dinv != nullptr, small);
+  const size_t smem = solve_smem_bytes(mixed, small);
   cudaError_t e = ensure_smem_attr(k, smem);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(k, dim3(P.A.nblocks), dim3(kBlock), args, smem, s);

@@ -42,11 +42,13 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
   __syncwarp();
 }
 
-// Systems whose CTAs hold at most this many rows (small, L2-resident shares)
-// use the kernels that update x behind the barrier of the r.r sum, where the
-// wait is longer than the update; larger shares update x together with p
-// (one pass over p).  Both compute the same bits.
-constexpr int kSideXRows = 8192;
+// Systems whose CTAs hold at most kLocalRows rows each (small, L2-resident
+// shares), solved in one launch, use the small-share kernels: r of the CTA's
+// rows lives in shared memory (only the owning CTA ever reads it; three
+// accesses per step), and x is updated behind the barrier of the r.r sum,
+// where the wait is longer than the update.  Larger shares keep r in global
+// memory and update x together with p (one pass over p).  Both compute the
+// same bits.
 
 // Rows per thread in flight in the vector phases (all loads of a batch
 // issued before any is used): as many as the registers that the product
@@ -59,8 +61,9 @@ __host__ __device__ constexpr int vec_rows() {
 
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
-// launch saved, for at most P.chunk_iters steps.  kSideX: x is updated by
-// warps 1.. behind the barrier of the r.r sum (see kSideXRows).
+// launch saved, for at most P.chunk_iters steps.  kSideX: the small-share
+// kernel (above): r in shared memory, x updated by warps 1.. behind the
+// barrier of the r.r sum; it runs a solve in one launch.
 //
 // Scalars live in the CTA state in shared memory (thread 0 updates them
 // between CTA barriers; every thread reads them after one), so that the
@@ -80,6 +83,12 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   double* __restrict__ p = P.p;
   ConsumerCursor cur;
   constexpr int kVR = vec_rows<kJacobi, kSideX>();
+  // r_i of the CTA's rows: shared memory in the small-share kernel
+  double* const r_loc = sm.local() - row0;
+  auto R = [&](int i) -> double& {
+    if constexpr (kSideX) return r_loc[i];
+    else return r[i];
+  };
 
   // Group-wide sum of nv values per thread (nv <= 3), fused with the vote of
   // the consumer warps (`ok`: this thread's waits all succeeded).  Each warp
@@ -193,7 +202,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       const double ri = bi - s;
       double zi = ri;
       if constexpr (kJacobi) zi = P.dinv[i] * ri;
-      r[i] = ri;
+      R(i) = ri;
       p[i] = zi;
       if constexpr (kMixed) P.p32[i] = static_cast<float>(zi);
       acc_rr = fma(ri, ri, acc_rr);
@@ -274,7 +283,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         const int i = base + u * kConsumers;
         if (i < row1) {
           qv[u] = P.q[i];
-          rv[u] = r[i];
+          rv[u] = R(i);
           if constexpr (kJacobi) dv[u] = P.dinv[i];
         }
       }
@@ -283,7 +292,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         const int i = base + u * kConsumers;
         if (i < row1) {
           const double rn = fma(-alpha, qv[u], rv[u]);
-          r[i] = rn;
+          R(i) = rn;
           acc_r = fma(rn, rn, acc_r);
           if constexpr (kJacobi) acc_z = fma(rn, dv[u] * rn, acc_z);
         }
@@ -342,7 +351,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       double acc_t = 0.0, acc_tz = 0.0;
       auto epi = [&](int i, double s, double bi) {
         const double ri = bi - s;
-        r[i] = ri;
+        R(i) = ri;
         acc_t = fma(ri, ri, acc_t);
         if constexpr (kJacobi) acc_tz = fma(ri, P.dinv[i] * ri, acc_tz);
       };
@@ -358,7 +367,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       }
       if (st->flags & kFlagDone) break;
       for (int i = row0 + tid; i < row1; i += kConsumers) {
-        double zi = r[i];
+        double zi = R(i);
         if constexpr (kJacobi) zi = P.dinv[i] * zi;
         const double pi = fma(beta, p[i], zi);
         p[i] = pi;
@@ -377,7 +386,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           const int i = base + u * kConsumers;
           if (i < row1) {
             pv[u] = p[i];
-            zv[u] = r[i];
+            zv[u] = R(i);
             if constexpr (kJacobi) zv[u] = P.dinv[i] * zv[u];
           }
         }
@@ -400,7 +409,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
           const int i = base + u * kConsumers;
           if (i < row1) {
             pv[u] = p[i];
-            zv[u] = r[i];
+            zv[u] = R(i);
             if constexpr (kJacobi) zv[u] = P.dinv[i] * zv[u];
             xv[u] = x[i];
           }

@@ -1,8 +1,8 @@
 """Solver paths that the finite-element systems do not reach, through the C
 ABI: the mixed-precision product on rows of two-lanes-per-row and whole-warp
 steps (rows of 33-64 and of more than 64 entries), and explicit CTA counts of
-the persistent kernel (one CTA: no group barrier at all; a few CTAs; the
-automatic choice)."""
+the persistent kernel (one CTA: no group barrier at all, and a share too
+large for the small-share kernel; a few CTAs; the automatic choice)."""
 import numpy as np
 import pytest
 
@@ -50,6 +50,12 @@ def test_cta_counts(ctas):
             assert h.nblocks == ctas
         else:
             assert 1 <= h.nblocks
+        # one CTA holds all 2744 rows: the kernel with r in global memory;
+        # more CTAs: the small-share kernel (r in shared memory)
+        max_rows, small = h.partition_info()
+        assert max_rows == (A.n if ctas == 1 else max_rows) and max_rows >= -(-A.n // h.nblocks)
+        assert small == (max_rows <= 2560)
+        assert small == (ctas != 1)
         res, x = _solve(h, b)
     assert res.status == cg.CG_OK and res.relres <= TOL
     ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
