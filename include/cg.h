@@ -198,11 +198,13 @@ int cg_dot_noalloc(int64_t n, const double* x, const double* y, double* result, 
 
 /*
  * Self-test of the library's bounded device-side waits (no paper
- * counterpart): launches a one-CTA kernel that waits at a grid barrier no
- * other CTA will reach.  The wait must give up after limit_ms and the kernel
- * must report CG_ETIMEOUT, leaving the CUDA context usable.  *kernel_status
- * receives the status the kernel wrote.  Runs on the current device and the
- * legacy default stream; synchronous.
+ * counterpart): launches a one-CTA kernel whose thread 0 waits at the solves'
+ * group barrier for a group of two CTAs that no other CTA joins.  The wait
+ * must give up after limit_ms, raise the solve's abort flag and report
+ * CG_ETIMEOUT, leaving the CUDA context usable.  *kernel_status receives the
+ * status the kernel wrote; the call returns CG_ECUDA if the wait gave up
+ * without raising the abort flag.  Runs on the current device and the legacy
+ * default stream; synchronous.
  */
 int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status);
 

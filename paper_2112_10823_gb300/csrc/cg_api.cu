@@ -573,6 +573,8 @@ int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status) {
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_selftest_wait_timeout");
   *kernel_status = hc.status;
+  if (hc.status == CG_ETIMEOUT && (hc.abort != 1 || hc.timeout_site != cgk::kSelftestSite))
+    return fail(nullptr, CG_ECUDA, "cg_selftest_wait_timeout: the wait gave up without raising the abort flag");
   return CG_OK;
 }
 

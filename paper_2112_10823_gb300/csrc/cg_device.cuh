@@ -29,12 +29,6 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Orders this thread's earlier generic-proxy shared-memory accesses (made
-// visible to it by a CTA barrier) before later async-proxy writes.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
@@ -62,15 +56,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
-__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) {
   return *reinterpret_cast<const volatile int32_t*>(p);
@@ -308,74 +294,8 @@ __device__ __forceinline__ bool group_barrier_t0(SolveCtrl* ctrl, unsigned long 
   return true;
 }
 
-// ----------------------------------------------------------- group barrier
-
-// Bounded barrier of the `count` CTAs that solve one system together (the
-// whole grid of a single-system solve, a group of CTAs in a batched solve;
-// all co-resident: the launch is cooperative).  Split in an arrive and a wait
-// half so that a CTA can do independent work between them.  Thread 0 of each
-// CTA adds one arrival to the system's monotonic 64-bit counter with release
-// semantics and later spins with acquire loads until all CTAs of this round
-// have arrived; the fence afterwards makes every write that preceded any
-// CTA's arrival visible to all threads of this CTA.  A wait longer than
-// `limit_ns`, or an abort raised by another CTA, makes wait() return false in
-// every thread of the CTA (the caller then abandons the solve).  A group of
-// one CTA needs only the CTA barrier.
-struct GridBarrier {
-  unsigned long long target = 0;  // counter value that completes the current round
-  unsigned int count = 1;         // CTAs in the group
-
-  // All threads call; the CTA's writes before this point are published.
-  __device__ __forceinline__ void arrive(SolveCtrl* ctrl) {
-    cta_sync();
-    target += count;
-    if (count > 1 && threadIdx.x == 0) {
-      __threadfence();
-      red_release_add_u64(&ctrl->barrier, 1ull);
-    }
-  }
-
-  __device__ __forceinline__ bool wait(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
-                                       int32_t* flag_smem) {
-    if (count <= 1) return true;  // arrive() already synchronised the CTA
-    if (threadIdx.x == 0) {
-      int32_t ok = 1;
-      unsigned long long t0 = 0;
-      uint32_t spins = 0;
-      while (ld_acquire_u64(&ctrl->barrier) < target) {
-        if ((++spins & 255u) == 0) {
-          if (ld_volatile_i32(&ctrl->abort)) { ok = 0; break; }
-          unsigned long long now = global_timer_ns();
-          if (t0 == 0) t0 = now;
-          else if (now - t0 > limit_ns) {
-            atomicExch(&ctrl->abort, 1);
-            atomicExch(&ctrl->timeout_site, site);
-            ok = 0;
-            break;
-          }
-        }
-      }
-      __threadfence();
-      *flag_smem = ok;
-    }
-    cta_sync();
-    return *flag_smem != 0;
-  }
-
-  __device__ __forceinline__ bool sync(SolveCtrl* ctrl, unsigned long long limit_ns, int site,
-                                       int32_t* flag_smem) {
-    arrive(ctrl);
-    return wait(ctrl, limit_ns, site, flag_smem);
-  }
-};
-
 // ------------------------------------------------------ streamed CSR product
 
-// Shared memory of a solve or product CTA: the value ring (sized for FP64;
-// FP32 values use its first half) and the column-index ring, each followed by
-// its kMirror-entry mirror, the full/empty mbarriers of every slot, the CTA
-// state of a solve, the warp partials of its sums, and a few words (stop
-// flag).
 // Per-CTA state of a solve, in shared memory: written by thread 0 (between
 // CTA barriers), read by all.  Keeping it out of registers leaves the
 // product in the step loop the registers it needs.
@@ -404,9 +324,11 @@ struct SumScratch {
 };
 
 // Dynamic shared memory of a persistent CTA: the value ring (values of vb
-// bytes: 8 for FP64, 4 for FP32, so that an FP32 stream leaves the rest of
-// the SM's 256 KB to L1 for the gathers), the column ring, the slots'
-// mbarriers, the CTA state of a solve, the warp partials of its sums.
+// bytes: 8 for FP64, 4 for FP32, so that an FP32 stream leaves more of the
+// SM's 256 KB to L1 for the gathers) and the column-index ring, each followed
+// by its kMirror-entry mirror, the full/empty mbarriers of every slot, the
+// CTA state of a solve, the warp partials of its sums, a few words (stop
+// flag), and in the small-share solve the r of the CTA's rows.
 struct RingSmem {
   static constexpr int kRingAlloc = kRing + kMirror;
   static constexpr size_t kColBytes = sizeof(int32_t) * kRingAlloc;

@@ -158,6 +158,8 @@ cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblo
 int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
+// timeout_site the self-test's wait records
+constexpr int32_t kSelftestSite = 99;
 // Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed;
 // `local`: the small-share kernels, with r of the share).
 size_t solve_smem_bytes(bool mixed, bool local = false);

@@ -167,22 +167,21 @@ cudaError_t launch_jacobi_dinv(const int32_t* row_ptr, const int32_t* col_idx, c
   return cudaGetLastError();
 }
 
-// ---- self-test of the bounded wait: one CTA (of kConsumers threads, the
-// group barrier's CTA size) waits at a group barrier of two CTAs, so the wait
-// must run out after limit_ns and report kETIMEOUT through the control block.
+// ---- self-test of the bounded wait: thread 0 of one CTA arrives at the
+// group barrier of the solves (group_barrier_t0) for a group of two CTAs that
+// no other CTA joins, so its wait must run out after limit_ns, raise the
+// abort flag, record the site and report kETIMEOUT through the control block.
 __global__ void wait_timeout_selftest_kernel(SolveCtrl* ctrl, unsigned long long limit_ns) {
-  __shared__ int32_t flag;
-  GridBarrier gb;
-  gb.count = 2;  // the barrier below waits for 2 arrivals; only 1 CTA exists
-  if (!gb.sync(ctrl, limit_ns, 99, &flag)) {
-    if (threadIdx.x == 0) ctrl->status = kETIMEOUT;
-  } else if (threadIdx.x == 0) {
-    ctrl->status = kOK;
+  __shared__ unsigned long long target;
+  if (threadIdx.x == 0) {
+    target = 0;
+    const bool ok = group_barrier_t0(ctrl, &target, 2u, limit_ns, kSelftestSite);
+    ctrl->status = ok ? kOK : kETIMEOUT;
   }
 }
 
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s) {
-  wait_timeout_selftest_kernel<<<1, kConsumers, 0, s>>>(ctrl, limit_ns);
+  wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(ctrl, limit_ns);
   return cudaGetLastError();
 }
 
