@@ -119,3 +119,15 @@ def test_batch_without_gpu_fails_loudly(built):
     with pytest.raises(cg.CGError) as e:
         cg.Batch()
     assert e.value.status in (cg.CG_ECUDA, cg.CG_ENOMEM)
+
+
+def test_null_handle_queries_rejected(built):
+    """The handle queries refuse a NULL handle with CG_EINVAL (no GPU involved)."""
+    import ctypes
+    import paper_2112_10823_gb300 as cg
+    lib = cg.lib
+    i32, i64 = ctypes.c_int32(0), ctypes.c_int64(0)
+    assert lib.cg_info(None, ctypes.byref(i64), None, None) == cg.CG_EINVAL
+    assert lib.cg_partition_info(None, ctypes.byref(i32), ctypes.byref(i32)) == cg.CG_EINVAL
+    assert b"NULL handle" in lib.cg_last_error(None)
+    assert lib.cg_selftest_wait_timeout(0, ctypes.byref(i32)) == cg.CG_EINVAL
