@@ -32,7 +32,7 @@ namespace cgk {
 
 // One system on the whole grid: CTA c is rank c of the group.  kJacobi:
 // preconditioned by M = diag(A) (P.dinv).
-template <bool kMixed, bool kJacobi, bool kSideX>
+template <bool kMixed, bool kJacobi, bool kSmallShare>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw, kMixed ? 4u : 8u};  // the step loop streams FP32 values in the mixed solve
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
     solve_producer<kMixed>(sm, cs, P);
     return;
   }
-  solve_consumers<kMixed, kJacobi, kSideX>(sm, cs, P, blockIdx.x);
+  solve_consumers<kMixed, kJacobi, kSmallShare>(sm, cs, P, blockIdx.x);
 }
 
 // y = A x (same partition and stream as the solve; one pass).
@@ -79,7 +79,7 @@ cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
   int max_sm = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e == cudaSuccess && max_sm > 0) {
-    // a hint: the driver rounds it up to a configuration the launch fits in
+    // a hint: CUDA picks the nearest supported carveout that the launch fits in
     const size_t need = bytes + 1024;  // + the CTA's reserved shared memory
     int pct = static_cast<int>((need * 100 + static_cast<size_t>(max_sm) - 1) / static_cast<size_t>(max_sm));
     if (pct > 100) pct = 100;
@@ -97,16 +97,16 @@ cudaError_t launch_spmv(const DevCsr& A, const double* x, double* y, int32_t* er
   return cudaGetLastError();
 }
 
-template <bool kSideX>
+template <bool kSmallShare>
 const void* solve_kernel_ptr_t(bool mixed, bool jacobi) {
-  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<true, true, kSideX>)
-                           : reinterpret_cast<const void*>(cg_solve_kernel<true, false, kSideX>);
-  return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<false, true, kSideX>)
-                : reinterpret_cast<const void*>(cg_solve_kernel<false, false, kSideX>);
+  if (mixed) return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<true, true, kSmallShare>)
+                           : reinterpret_cast<const void*>(cg_solve_kernel<true, false, kSmallShare>);
+  return jacobi ? reinterpret_cast<const void*>(cg_solve_kernel<false, true, kSmallShare>)
+                : reinterpret_cast<const void*>(cg_solve_kernel<false, false, kSmallShare>);
 }
 
-const void* solve_kernel_ptr(bool mixed, bool jacobi, bool side_x = false) {
-  return side_x ? solve_kernel_ptr_t<true>(mixed, jacobi) : solve_kernel_ptr_t<false>(mixed, jacobi);
+const void* solve_kernel_ptr(bool mixed, bool jacobi, bool small_share = false) {
+  return small_share ? solve_kernel_ptr_t<true>(mixed, jacobi) : solve_kernel_ptr_t<false>(mixed, jacobi);
 }
 
 size_t solve_smem_bytes(bool mixed, bool local) {

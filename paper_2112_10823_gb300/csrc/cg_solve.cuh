@@ -54,21 +54,21 @@ __device__ __forceinline__ void solve_producer(const RingSmem& sm, const CtaStre
 // issued before any is used): as many as the registers that the product
 // leaves allow without spilling (128 per thread at 16 warps per CTA; the
 // Jacobi variants carry dinv as well, the fused x and p update three vectors).
-template <bool kJacobi, bool kSideX>
+template <bool kJacobi, bool kSmallShare>
 __host__ __device__ constexpr int vec_rows() {
-  return kSideX ? (kJacobi ? 3 : 4) : (kJacobi ? 2 : 3);
+  return kSmallShare ? (kJacobi ? 3 : 4) : (kJacobi ? 2 : 3);
 }
 
 // Consumer side of a solve task: share `rank` (of P.group CTAs) of the CG
 // iteration on one system, from its start or from the state a previous
-// launch saved, for at most P.chunk_iters steps.  kSideX: the small-share
+// launch saved, for at most P.chunk_iters steps.  kSmallShare: the small-share
 // kernel (above): r in shared memory, x updated by warps 1.. behind the
 // barrier of the r.r sum; it runs a solve in one launch.
 //
 // Scalars live in the CTA state in shared memory (thread 0 updates them
 // between CTA barriers; every thread reads them after one), so that the
 // registers of the step loop's product are the product's own.
-template <bool kMixed, bool kJacobi, bool kSideX>
+template <bool kMixed, bool kJacobi, bool kSmallShare>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
                                                 const int rank) {
   const DevCsr& A = P.A;
@@ -82,11 +82,11 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   double* __restrict__ r = P.r;
   double* __restrict__ p = P.p;
   ConsumerCursor cur;
-  constexpr int kVR = vec_rows<kJacobi, kSideX>();
+  constexpr int kVR = vec_rows<kJacobi, kSmallShare>();
   // r_i of the CTA's rows: shared memory in the small-share kernel
   double* const r_loc = sm.local() - row0;
   auto R = [&](int i) -> double& {
-    if constexpr (kSideX) return r_loc[i];
+    if constexpr (kSmallShare) return r_loc[i];
     else return r[i];
   };
 
@@ -298,10 +298,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         }
       }
     }
-    // kSideX: x += alpha p by warps 1.. while warp 0 does the sum below (x is
+    // kSmallShare: x += alpha p by warps 1.. while warp 0 does the sum below (x is
     // needed again only by the next residual replacement or at the end)
     auto side_x = [&] {
-      if constexpr (kSideX) {
+      if constexpr (kSmallShare) {
         for (int base = row0 + tid - 32; base < row1; base += 2 * (kConsumers - 32)) {
           double pv[2], xv[2];
 #pragma unroll
@@ -345,7 +345,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     if (f & kFlagReplace) {
       // x += alpha p (unless done behind the sum), then r = b - A x in FP64
       // (residual replacement); r, rr and rho take the true residual's values
-      if constexpr (!kSideX)
+      if constexpr (!kSmallShare)
         for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
       if (!group_sync()) { solve_fail(sm, P); return; }
       double acc_t = 0.0, acc_tz = 0.0;
@@ -374,10 +374,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         if constexpr (kMixed) P.p32[i] = static_cast<float>(pi);
       }
     } else if (f & kFlagDone) {
-      if constexpr (!kSideX)
+      if constexpr (!kSmallShare)
         for (int i = row0 + tid; i < row1; i += kConsumers) x[i] = fma(alpha, p[i], x[i]);
       break;
-    } else if constexpr (kSideX) {
+    } else if constexpr (kSmallShare) {
       // ---- p = z + beta p   (z = dinv .* r, or r; x was updated behind the sum)
       for (int base = row0 + tid; base < row1; base += kVR * kConsumers) {
         double pv[kVR], zv[kVR];
