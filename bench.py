@@ -495,8 +495,16 @@ def run_ours(args):
     e2e = {"value": whole_job_rate(args.steps, world, t_e2e), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
            "d2h_bytes_per_step": 8 * n}
 
-    # ---- latency percentiles and board energy over back-to-back solves
+    # ---- latency percentiles and board energy over back-to-back solves, and
+    # the idle board power (nothing running) over half a second just before
     energy = Energy(local)
+    torch.cuda.synchronize()
+    idle_watts = None
+    i0, ti0 = energy.read_j(), time.perf_counter()
+    time.sleep(0.5)
+    i1, ti = energy.read_j(), time.perf_counter() - ti0
+    if i0 is not None and i1 is not None:
+        idle_watts = (i1 - i0) / ti
     lat = []
     e0 = energy.read_j()
     tl0 = time.perf_counter()
@@ -614,7 +622,10 @@ def run_ours(args):
         "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm_peak, "ms": spmv_ms, "bytes": spmv_bytes(n, nnz),
                  "l2": "flushed before every call", "precision": "fp64"},
         "blas1": {k: dict(v, frac=v["gbs"] / hbm_peak) for k, v in blas1.items()},
-        "energy": {"joules_per_solve": joules, "avg_watts": watts, "source": "NVML board energy",
+        "energy": {"joules_per_solve": joules, "avg_watts": watts, "idle_watts": idle_watts,
+                   "joules_per_solve_above_idle": (joules - idle_watts * tl / args.latency_solves
+                                                   if joules is not None and idle_watts is not None else None),
+                   "source": "NVML board energy",
                    "solves": args.latency_solves},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "solves": len(lat)},

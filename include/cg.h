@@ -141,6 +141,14 @@ int cg_spmv(cg_handle h, const double* x, double* y);
  */
 int cg_dot(cg_handle h, int64_t n, const double* x, const double* y, double* result);
 
+/*
+ * cg_dot with the sum returned in host memory: the same kernel (the same
+ * bits) on the handle's stream, into a device scalar the handle owns; the
+ * call then waits for the stream and writes the sum to *result (host
+ * memory).  Synchronous; for tests and callers without a device buffer.
+ */
+int cg_dot_host(cg_handle h, int64_t n, const double* x, const double* y, double* result);
+
 /* y <- a x + y over n elements (Sec. 5.2 "addition of vectors"), FMA.
  * Device pointers; x and y must not overlap.  Asynchronous. */
 int cg_axpy(cg_handle h, int64_t n, double a, const double* x, double* y);

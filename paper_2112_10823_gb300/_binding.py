@@ -95,6 +95,8 @@ def _load() -> ctypes.CDLL:
     lib.cg_spmv.argtypes = [vp, vp, vp]
     lib.cg_dot.restype = ctypes.c_int
     lib.cg_dot.argtypes = [vp, i64, vp, vp, vp]
+    lib.cg_dot_host.restype = ctypes.c_int
+    lib.cg_dot_host.argtypes = [vp, i64, vp, vp, P(ctypes.c_double)]
     lib.cg_axpy.restype = ctypes.c_int
     lib.cg_axpy.argtypes = [vp, i64, dbl, vp, vp]
     lib.cg_ewmul.restype = ctypes.c_int
@@ -283,6 +285,16 @@ def cg_dot(h: Handle, x, y, out, n: int | None = None) -> None:
     _check_f64("y", y, n)
     _check_f64("out", out, 1)
     _check(lib.cg_dot(h._h, n, _ptr(x), _ptr(y), _ptr(out)), h._h)
+
+
+def cg_dot_host(h: Handle, x, y, n: int | None = None) -> float:
+    """x . y (CUDA float64 tensors) returned to the host; synchronous."""
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    r = ctypes.c_double(float("nan"))
+    _check(lib.cg_dot_host(h._h, n, _ptr(x), _ptr(y), ctypes.byref(r)), h._h)
+    return r.value
 
 
 def cg_dot_noalloc(x, y, out, n: int | None = None, stream=None) -> None:

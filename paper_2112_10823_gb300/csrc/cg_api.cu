@@ -128,6 +128,7 @@ struct cg_ctx {
   cgk::SolveCtrl* d_ctrl = nullptr;
   double* d_dot_partials = nullptr;
   unsigned int* d_dot_counter = nullptr;
+  double* d_dot_result = nullptr;  // cg_dot_host's device scalar
   int32_t* d_err = nullptr;
   cgk::SolveCtrl* h_ctrl = nullptr;  // pinned
   std::vector<void*> allocs;
@@ -367,6 +368,7 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(dalloc(h, &h->d_ctrl, 1), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_partials, static_cast<size_t>(4) * sms + 8), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_counter, 4), "cg_create: cudaMalloc");
+  CG_TRY(dalloc(h, &h->d_dot_result, 1), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_err, 4), "cg_create: cudaMalloc");
   if (o.precision == CG_PREC_MIXED) {
     CG_TRY(dalloc(h, &h->d_val32, nnz + pad), "cg_create: cudaMalloc");
@@ -462,6 +464,19 @@ int cg_dot(cg_handle h, int64_t n, const double* x, const double* y, double* res
   const int grid = cgk::dot_grid(n, h->num_sms);
   cudaError_t e = cgk::launch_dot(n, x, y, result, h->d_dot_partials, h->d_dot_counter, grid, h->stream);
   return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_dot: launch");
+}
+
+int cg_dot_host(cg_handle h, int64_t n, const double* x, const double* y, double* result) {
+  if (!h) return fail(nullptr, CG_EINVAL, "cg_dot_host: NULL handle");
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_dot_host: bad arguments");
+  DeviceGuard g(h->device);
+  const int grid = cgk::dot_grid(n, h->num_sms);
+  cudaError_t e =
+      cgk::launch_dot(n, x, y, h->d_dot_result, h->d_dot_partials, h->d_dot_counter, grid, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(result, h->d_dot_result, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_dot_host");
 }
 
 int cg_axpy(cg_handle h, int64_t n, double a, const double* x, double* y) {

@@ -131,3 +131,5 @@ def test_null_handle_queries_rejected(built):
     assert lib.cg_partition_info(None, ctypes.byref(i32), ctypes.byref(i32)) == cg.CG_EINVAL
     assert b"NULL handle" in lib.cg_last_error(None)
     assert lib.cg_selftest_wait_timeout(0, ctypes.byref(i32)) == cg.CG_EINVAL
+    d = ctypes.c_double(0.0)
+    assert lib.cg_dot_host(None, 0, None, None, ctypes.byref(d)) == cg.CG_EINVAL

@@ -42,6 +42,8 @@ def test_dot(h, n):
     out2 = torch.zeros_like(out)
     cg.cg_dot(h, _cuda(x), _cuda(y), out2, n=n)
     assert out2.item() == got
+    # the host-result call runs the same kernel: the same bits
+    assert cg.cg_dot_host(h, _cuda(x), _cuda(y), n=n) == got
 
 
 def test_dot_integers_exact(h):
