@@ -762,13 +762,21 @@ def run_batch(args):
     def step_host():
         reqs = [cg.Request(hs["rp"], hs["ci"], hs["va"], hs["b"], hs["x"], tol=TOL, maxit=10 * s_["n"], tag=i)
                 for i, (hs, s_) in enumerate(zip(hosts, systems))]
-        res = bt.wait_all(bt.submit(reqs))
-        assert all(r.status == cg.CG_OK and r.relres <= TOL for r in res)
+        res_h = bt.wait_all(bt.submit(reqs))
+        assert all(r.status == cg.CG_OK and r.relres <= TOL for r in res_h)
+        return res_h
 
     step_host()
     te0 = time.perf_counter()
+    spans = []
     for _ in range(args.steps):
-        step_host()
+        res_h = step_host()
+        # where an end-to-end step goes: admission (host checks, partition,
+        # copies) from the first submit to the last system resident, then the
+        # round and the copies of x back
+        sub0 = min(r.submit_ms for r in res_h)
+        adm1 = max(r.admit_ms for r in res_h)
+        spans.append((adm1 - sub0, max(r.done_ms for r in res_h) - adm1))
     t_e2e = time.perf_counter() - te0
     dev_s = (st1["round_ms_total"] - st0["round_ms_total"]) / 1000.0
     value = count * args.steps / dev_s
@@ -806,6 +814,8 @@ def run_batch(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "note": "wall clock through cg_batch_submit/wait with every system's CSR arrays and b in pinned "
                         "host memory (admission copies them to the device) and x read back to the host",
+                "admission_ms": float(np.mean([a for a, _ in spans])),
+                "round_and_readback_ms": float(np.mean([r for _, r in spans])),
                 "device_resident_inputs_solves_per_s": count * args.steps / t_wall},
         "gpu_launches": int(rounds + (count * args.steps if mixed else 0)),
         "clocks": clk.summary(),

@@ -164,6 +164,42 @@ struct Job {
 
 }  // namespace
 
+// Pinned host memory for the small per-system arrays of an admission pass
+// (row pointers, step partition, rebased columns), so that every upload is
+// an asynchronous copy from pinned memory; chunks are kept and reused, and
+// reset() starts a new pass once the previous pass's copies have completed.
+struct PinnedPool {
+  struct Chunk {
+    char* p;
+    size_t size, used;
+  };
+  std::vector<Chunk> chunks;
+  ~PinnedPool() {
+    for (auto& c : chunks) cudaFreeHost(c.p);
+  }
+  void reset() {
+    for (auto& c : chunks) c.used = 0;
+  }
+  // bytes of pinned memory (16-byte aligned), or nullptr if none can be had
+  void* take(size_t bytes) {
+    bytes = (bytes + 15) & ~size_t(15);
+    for (auto& c : chunks)
+      if (c.size - c.used >= bytes) {
+        void* q = c.p + c.used;
+        c.used += bytes;
+        return q;
+      }
+    const size_t size = std::max(bytes, size_t(8) << 20);
+    char* q = nullptr;
+    if (cudaMallocHost(&q, size) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    chunks.push_back({q, size, bytes});
+    return q;
+  }
+};
+
 struct cg_batch_ctx {
   int device = 0;
   bool mixed = false;
@@ -189,8 +225,9 @@ struct cg_batch_ctx {
   cgk::SolveCtrl* d_ctrl = nullptr;
   cgk::BatchQueue* d_queue = nullptr;
   int32_t* d_next = nullptr;
-  int32_t* d_admit_err = nullptr;      // Jacobi: first row without a positive diagonal (+1)
-  int32_t* h_admit_err = nullptr;      // pinned
+  int32_t* d_admit_err = nullptr;      // per slot, Jacobi: first row without a positive diagonal (+1)
+  int32_t* h_admit_err = nullptr;      // pinned, per slot
+  PinnedPool staging;                  // host arrays of the admission pass in flight
   cgk::SolveParams* h_sys = nullptr;   // pinned
   cgk::SolveCtrl* h_ctrl = nullptr;    // pinned
   cgk::BatchQueue* h_queue = nullptr;  // pinned
@@ -348,9 +385,33 @@ void finish_without_device(cg_batch_ctx* b, Job* j, int status) {
 }
 
 // Prepare and upload the queue head while memory and slots allow.  Called by
-// the worker without the lock held (the lock guards the queue only).
+// the worker without the lock held (the lock guards the queue only).  The
+// copies of every system of the pass go onto the copy stream back to back
+// (the host prepares the next system while the previous one's copies run);
+// the small host arrays are staged in pinned memory that stays untouched
+// until the one synchronisation at the end of the pass, after which each
+// system is checked and made resident.
 void admit(cg_batch_ctx* b) {
-  std::vector<Job*> uploaded;
+  struct Staged {
+    Job* j;
+    cudaError_t e;
+  };
+  std::vector<Staged> staged;
+  b->staging.reset();  // the previous pass ended with a synchronisation
+  cudaStream_t s = b->copy;
+  // host -> device from pinned staging (a copy the host may overwrite only
+  // after the pass's synchronisation); without pinned memory, from src, and
+  // the stream is drained before src can go away
+  auto upload = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    void* q = b->staging.take(bytes);
+    if (q == nullptr) {
+      cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+      return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    std::memcpy(q, src, bytes);
+    return cudaMemcpyAsync(dst, q, bytes, cudaMemcpyHostToDevice, s);
+  };
   for (;;) {
     Job* j = nullptr;
     {
@@ -395,26 +456,29 @@ void admit(cg_batch_ctx* b) {
     char* base = b->d_arena + off;
     auto at = [&](size_t o) { return base + o; };
     const size_t pad = cgk::kPadEntries;
-    cudaStream_t s = b->copy;
     cudaError_t e = cudaSuccess;
     auto step = [&](cudaError_t x) {
       if (e == cudaSuccess) e = x;
     };
-    step(cudaMemcpyAsync(at(L.rp), rp.data(), 4 * (n + 1), cudaMemcpyHostToDevice, s));
+    step(upload(at(L.rp), rp.data(), 4 * (n + 1)));
     step(cudaMemsetAsync(at(L.col), 0, 4 * (nnz + pad), s));
     step(cudaMemsetAsync(at(L.val), 0, 8 * (nnz + pad), s));
     if (nnz > 0) {
+      // the request's own arrays stay valid until its result is final
       const cudaMemcpyKind k = r.csr.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-      if (r.csr.index_base == 0 || ci.empty()) {
+      if (r.csr.index_base == 0) {
         step(cudaMemcpyAsync(at(L.col), r.csr.col_idx, 4 * nnz, k, s));
-      }
-      if (r.csr.index_base != 0) {
-        if (ci.empty()) {  // device input without validation: bring the columns over to rebase them
-          ci.resize(static_cast<size_t>(nnz));
-          step(cudaMemcpy(ci.data(), r.csr.col_idx, 4 * nnz, cudaMemcpyDeviceToHost));
+      } else {
+        if (ci.empty()) {  // not validated: the columns are not on the host yet
+          if (r.csr.on_device) {
+            ci.resize(static_cast<size_t>(nnz));
+            step(cudaMemcpy(ci.data(), r.csr.col_idx, 4 * nnz, cudaMemcpyDeviceToHost));
+          } else {
+            ci.assign(r.csr.col_idx, r.csr.col_idx + nnz);
+          }
         }
         for (auto& v : ci) v -= 1;
-        step(cudaMemcpyAsync(at(L.col), ci.data(), 4 * nnz, cudaMemcpyHostToDevice, s));
+        step(upload(at(L.col), ci.data(), 4 * nnz));
       }
       step(cudaMemcpyAsync(at(L.val), r.csr.val, 8 * nnz, k, s));
       if (b->mixed) {
@@ -423,22 +487,23 @@ void admit(cg_batch_ctx* b) {
                                     s));
       }
     }
-    step(cudaMemcpyAsync(at(L.step), part.step.data(), sizeof(int4) * part.step.size(), cudaMemcpyHostToDevice, s));
-    step(cudaMemcpyAsync(at(L.mode), part.step_mode.data(), 4 * part.step_mode.size(), cudaMemcpyHostToDevice, s));
-    step(cudaMemcpyAsync(at(L.bstep), part.block_step.data(), 4 * part.block_step.size(), cudaMemcpyHostToDevice, s));
-    step(cudaMemcpyAsync(at(L.brow), part.block_row.data(), 4 * part.block_row.size(), cudaMemcpyHostToDevice, s));
+    step(upload(at(L.step), part.step.data(), sizeof(int4) * part.step.size()));
+    step(upload(at(L.mode), part.step_mode.data(), 4 * part.step_mode.size()));
+    step(upload(at(L.bstep), part.block_step.data(), 4 * part.block_step.size()));
+    step(upload(at(L.brow), part.block_row.data(), 4 * part.block_row.size()));
     step(cudaMemcpyAsync(at(L.b), r.b, 8 * n, is_device_ptr(r.b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          s));
     step(cudaMemsetAsync(at(L.x), 0, 8 * n, s));
     if (b->jacobi) {
-      step(cudaMemsetAsync(b->d_admit_err, 0, sizeof(int32_t), s));
+      step(cudaMemsetAsync(b->d_admit_err + slot, 0, sizeof(int32_t), s));
       step(cgk::launch_jacobi_dinv(reinterpret_cast<int32_t*>(at(L.rp)), reinterpret_cast<int32_t*>(at(L.col)),
                                    reinterpret_cast<double*>(at(L.val)), n, reinterpret_cast<double*>(at(L.dinv)),
-                                   b->d_admit_err, s));
-      step(cudaMemcpyAsync(b->h_admit_err, b->d_admit_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                                   b->d_admit_err + slot, s));
+      step(cudaMemcpyAsync(b->h_admit_err + slot, b->d_admit_err + slot, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s));
     }
     step(cudaMemsetAsync(b->d_ctrl + slot, 0, sizeof(cgk::SolveCtrl), s));
-    cgk::SolveParams& P = b->h_sys[slot];
+    cgk::SolveParams& P = b->h_sys[slot];  // pinned; read by the copy below when it runs
     std::memset(&P, 0, sizeof(P));
     P.A.row_ptr = reinterpret_cast<int32_t*>(at(L.rp));
     P.A.col_idx = reinterpret_cast<int32_t*>(at(L.col));
@@ -470,17 +535,24 @@ void admit(cg_batch_ctx* b) {
     P.chunk_iters = b->chunk_iters;
     P.dinv = b->jacobi ? reinterpret_cast<double*>(at(L.dinv)) : nullptr;
     step(cudaMemcpyAsync(b->d_sys + slot, &P, sizeof(P), cudaMemcpyHostToDevice, s));
-    // the host vectors must outlive the copies
-    step(cudaStreamSynchronize(s));
     j->d_x = reinterpret_cast<double*>(at(L.x));
-    if (e == cudaSuccess && b->jacobi && *b->h_admit_err != 0) {
+    staged.push_back({j, e});
+  }
+  if (staged.empty()) return;
+  const cudaError_t es = cudaStreamSynchronize(s);
+  std::vector<Job*> uploaded;
+  for (const Staged& st : staged) {
+    Job* j = st.j;
+    const cudaError_t e = st.e != cudaSuccess ? st.e : es;
+    const int slot = j->slot;
+    if (e == cudaSuccess && b->jacobi && b->h_admit_err[slot] != 0) {
       std::lock_guard<std::mutex> lk(b->mu);
       b->arena.release(j->off, j->bytes);
       b->free_slots.push_back(slot);
       j->slot = -1;
       finish_without_device(b, j, CG_EINVAL);
       b->err = "request " + std::to_string(j->ticket) + ": Jacobi preconditioner: diagonal of row " +
-               std::to_string(*b->h_admit_err - 1) + " is not positive";
+               std::to_string(b->h_admit_err[slot] - 1) + " is not positive";
       b->cv_done.notify_all();
       continue;
     }
@@ -907,12 +979,13 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   if ((e = cudaMalloc(&b->d_sys, sizeof(cgk::SolveParams) * b->max_systems)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_ctrl, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_queue, b->queue_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_next, 16)) != cudaSuccess || (e = cudaMalloc(&b->d_admit_err, 16)) != cudaSuccess)
+      (e = cudaMalloc(&b->d_next, 16)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_admit_err, sizeof(int32_t) * b->max_systems)) != cudaSuccess)
     return fail_cuda(e, "cg_batch_create: tables");
   if ((e = cudaMallocHost(&b->h_sys, sizeof(cgk::SolveParams) * b->max_systems)) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_ctrl, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_queue, b->queue_bytes)) != cudaSuccess ||
-      (e = cudaMallocHost(&b->h_admit_err, 16)) != cudaSuccess)
+      (e = cudaMallocHost(&b->h_admit_err, sizeof(int32_t) * b->max_systems)) != cudaSuccess)
     return fail_cuda(e, "cg_batch_create: pinned tables");
   std::memset(b->h_queue, 0, b->queue_bytes);
   if ((e = cudaMemset(b->d_ctrl, 0, sizeof(cgk::SolveCtrl) * b->max_systems)) != cudaSuccess ||

@@ -82,6 +82,23 @@ def test_batch_matches_oracle_per_system():
         _check_vs_oracle(A, b, res, _x(req))
 
 
+@pytest.mark.parametrize("validate", [True, False])
+def test_one_based_input_from_host_and_device(validate):
+    """One-based CSR (the paper's IA/JA/AA indexing) from host and from device
+    memory, with and without the library's validation: rebased on admission,
+    so the same bits as the zero-based request."""
+    cg = cg_mod()
+    A, b = _system(7, 31)
+    B = fi.to_one_based(A)
+    with cg.Batch(validate=validate) as bt:
+        reqs = [_request(A, b, host=True), _request(B, b, host=True), _request(B, b, host=False)]
+        res = _wait_all(bt, bt.submit(reqs))
+    _check_vs_oracle(A, b, res[0], _x(reqs[0]))
+    for k in (1, 2):
+        assert res[k].status == cg.CG_OK and res[k].iters == res[0].iters, res[k]
+        assert np.array_equal(_x(reqs[k]), _x(reqs[0]))
+
+
 def test_alone_and_in_a_mix_give_the_same_bits():
     cg = cg_mod()
     A, b = _system(10, 77)
