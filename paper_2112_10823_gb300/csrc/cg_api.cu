@@ -125,7 +125,8 @@ struct cg_ctx {
   double* d_xbuf = nullptr;   // staging of host x
   double* d_bbuf = nullptr;   // staging of host b
   double* d_partials = nullptr;
-  cgk::SolveCtrl* d_ctrl = nullptr;
+  cgk::SolveCtrl* d_ctrl = nullptr;  // followed by the CTAs' epoch flags (one allocation, one memset per solve)
+  unsigned long long* d_flags = nullptr;
   double* d_dot_partials = nullptr;
   unsigned int* d_dot_counter = nullptr;
   double* d_dot_result = nullptr;  // cg_dot_host's device scalar
@@ -148,6 +149,12 @@ int fail(cg_ctx* h, int code, const std::string& msg) {
 int cuda_fail(cg_ctx* h, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   return fail(h, e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA, m);
+}
+
+// The control block of a solve followed by one epoch flag per CTA.
+constexpr size_t ctrl_flags_offset() { return (sizeof(cgk::SolveCtrl) + 15) & ~size_t(15); }
+size_t ctrl_block_bytes(int nblocks) {
+  return ctrl_flags_offset() + sizeof(unsigned long long) * static_cast<size_t>(nblocks > 0 ? nblocks : 1);
 }
 
 template <typename T>
@@ -365,7 +372,12 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(dalloc(h, &h->d_xbuf, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_bbuf, n), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_partials, static_cast<size_t>(6) * h->nblocks), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_ctrl, 1), "cg_create: cudaMalloc");
+  {
+    unsigned char* blk = nullptr;
+    CG_TRY(dalloc(h, &blk, ctrl_block_bytes(h->nblocks)), "cg_create: cudaMalloc");
+    h->d_ctrl = reinterpret_cast<cgk::SolveCtrl*>(blk);
+    h->d_flags = reinterpret_cast<unsigned long long*>(blk + ctrl_flags_offset());
+  }
   CG_TRY(dalloc(h, &h->d_dot_partials, static_cast<size_t>(4) * sms + 8), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_counter, 4), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_dot_result, 1), "cg_create: cudaMalloc");
@@ -522,7 +534,7 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
     if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: copy of x");
     dx = h->d_xbuf;
   }
-  e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(cgk::SolveCtrl), h->stream);
+  e = cudaMemsetAsync(h->d_ctrl, 0, ctrl_block_bytes(h->nblocks), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: memset");
   cgk::SolveParams P;
   P.A = dev_view(h);
@@ -542,6 +554,7 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   P.pad = 0;
   P.chunk_iters = 0;
   P.dinv = h->d_dinv;
+  P.flags = h->nblocks > 1 ? h->d_flags : nullptr;
   e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: cooperative launch");
   e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(cgk::SolveCtrl), cudaMemcpyDeviceToHost, h->stream);

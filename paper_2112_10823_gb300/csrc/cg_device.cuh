@@ -312,6 +312,7 @@ struct CtaState {
   int32_t site;                // diagnostics: group waits so far
   int32_t ok;                  // the last group sum or barrier succeeded
   int32_t flags;               // kFlag* below
+  int32_t dep_lo, dep_hi;      // CTAs whose rows this CTA's columns reach (columns first, then ranks)
 };
 enum : int32_t { kFlagDone = 1, kFlagBreakdown = 2, kFlagReplace = 4, kFlagResumed = 8 };
 

@@ -116,6 +116,12 @@ struct SolveParams {
   int32_t pad;
   int64_t chunk_iters;          // steps per launch (<= 0: until the solve ends)
   const double* dinv;           // Jacobi preconditioner 1/diag(A), or nullptr (plain CG)
+  // Single-system solves: one epoch flag per CTA (zeroed before the launch).
+  // In the large-share kernel a CTA publishes the step number in its flag
+  // after its p update and waits only for the CTAs whose rows its own rows'
+  // columns reach, instead of a barrier of the whole group.  nullptr (and
+  // the other kernels): the group barrier.
+  unsigned long long* flags;
 };
 
 // Batched solves: one persistent launch over many systems.  Every CTA takes
@@ -160,6 +166,8 @@ int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
 // timeout_site the self-test's wait records
 constexpr int32_t kSelftestSite = 99;
+// timeout_site of a single-system solve's wait for its neighbours' p
+constexpr int32_t kNeighborSite = 98;
 // Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed;
 // `local`: the small-share kernels, with r of the share).
 size_t solve_smem_bytes(bool mixed, bool local = false);

@@ -68,9 +68,13 @@ __host__ __device__ constexpr int vec_rows() {
 // Scalars live in the CTA state in shared memory (thread 0 updates them
 // between CTA barriers; every thread reads them after one), so that the
 // registers of the step loop's product are the product's own.
-template <bool kMixed, bool kJacobi, bool kSmallShare>
+template <bool kMixed, bool kJacobi, bool kSmallShare, bool kNeighborWait>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
                                                 const int rank) {
+  // kNeighborWait: the single-system kernel for large shares (P.flags set
+  // when the group has several CTAs); the small-share and batched kernels
+  // always use the group barrier.
+  const bool neighbor = kNeighborWait && P.flags != nullptr;
   const DevCsr& A = P.A;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = A.block_row[rank], row1 = A.block_row[rank + 1];
@@ -163,6 +167,52 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
     cta_sync();
     return st->ok != 0;
   };
+  // End of a step in a single-system solve (P.flags set): instead of a group
+  // barrier, the CTA publishes this step's number in its epoch flag once its
+  // p is written (release pattern as in the group barrier) and waits until
+  // the CTAs that own the columns its rows reach (ranks dep_lo..dep_hi) have
+  // published the same step: the next product gathers p only from them.
+  // Reusing p in place is safe: a CTA overwrites its p only after the r.r
+  // barrier of the step, which every CTA reaches after its product.
+  auto neighbor_sync = [&]() -> bool {
+    cta_sync();
+    if (warp == 0) {
+      const unsigned long long epoch = static_cast<unsigned long long>(st->k);
+      if (lane == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(P.flags + rank), "l"(epoch) : "memory");
+      }
+      bool good = true;
+      unsigned long long t0 = 0;
+      uint32_t spins = 0;
+      for (int q0 = st->dep_lo; q0 <= st->dep_hi && good; q0 += 32) {
+        const int q = q0 + lane;
+        if (q <= st->dep_hi && q != rank) {
+          for (;;) {
+            unsigned long long v;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(P.flags + q) : "memory");
+            if (v >= epoch) break;
+            if ((++spins & 255u) == 0) {
+              if (*reinterpret_cast<const volatile int32_t*>(&ctrl->abort)) { good = false; break; }
+              const unsigned long long now = global_timer_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > P.wait_limit_ns) {
+                atomicExch(&ctrl->abort, 1);
+                atomicExch(&ctrl->timeout_site, kNeighborSite);
+                good = false;
+                break;
+              }
+            }
+          }
+        }
+      }
+      good = __all_sync(0xffffffffu, good);
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      if (lane == 0) st->ok = good ? 1 : 0;
+    }
+    cta_sync();
+    return st->ok != 0;
+  };
   // Products outside the step loop (setup, the final true residual, the
   // mixed solve's residual replacements) read the FP64 values and columns
   // directly from global memory with a compact per-lane loop: they run once
@@ -192,8 +242,45 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
       st->rr = rel * rel * st->bnorm2;  // reported only (the next step recomputes it)
       st->flags = kFlagResumed;
     }
+    st->dep_lo = 0x7fffffff;  // smallest and largest column of the CTA's rows, first
+    st->dep_hi = -1;
   }
   cta_sync();
+  if (neighbor) {
+    // the CTAs whose p the product gathers: ranks owning the CTA's column range
+    int cmin = 0x7fffffff, cmax = -1;
+    for (int k = A.row_ptr[row0] + tid; k < A.row_ptr[row1]; k += kConsumers) {
+      const int c = A.col_idx[k];
+      cmin = min(cmin, c);
+      cmax = max(cmax, c);
+    }
+    cmin = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned int>(cmin)));
+    cmax = __reduce_max_sync(0xffffffffu, cmax);
+    if (lane == 0) {
+      atomicMin(&st->dep_lo, cmin);
+      atomicMax(&st->dep_hi, cmax);
+    }
+    cta_sync();
+    if (tid == 0) {
+      auto owner = [&](int c) {  // the rank whose row range holds row c
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (A.block_row[mid] <= c) lo = mid;
+          else hi = mid - 1;
+        }
+        return lo;
+      };
+      if (st->dep_hi < 0) {  // no entries: nothing to wait for
+        st->dep_lo = 1;
+        st->dep_hi = 0;
+      } else {
+        st->dep_lo = owner(st->dep_lo);
+        st->dep_hi = owner(st->dep_hi);
+      }
+    }
+    cta_sync();
+  }
   if (!(st->flags & kFlagResumed)) {
     // ---- setup: r = b - A x, z = dinv .* r (Jacobi) or r, p = z,
     //      rho = r.z, rr = r.r, ||b||^2
@@ -426,7 +513,10 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         }
       }
     }
-    if (!group_sync()) { solve_fail(sm, P); return; }
+    bool synced;
+    if constexpr (kNeighborWait) synced = neighbor ? neighbor_sync() : group_sync();
+    else synced = group_sync();
+    if (!synced) { solve_fail(sm, P); return; }
     if (st->k >= st->k_end && st->k < P.maxit) {
       // end of this launch's share of the solve: save the state (identical in
       // every CTA of the group; x, r, p are complete after the barrier)

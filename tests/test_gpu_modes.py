@@ -78,3 +78,35 @@ def test_cta_count_products_agree_bitwise():
             cg.cg_spmv(h, x, y)
             ys.append(y.cpu().numpy())
     assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+
+
+def _permuted(A, seed):
+    """P A P^T for a random permutation P: SPD, with each row's columns spread
+    over the whole matrix (every CTA gathers p from every other)."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.col_idx, A.row_ptr), shape=(A.n, A.n))
+    perm = np.random.default_rng(seed).permutation(A.n)
+    Mp = M[perm][:, perm].tocsr()
+    Mp.sort_indices()
+    return fi.CSR(Mp.indptr.astype(np.int32), Mp.indices.astype(np.int32), Mp.data.astype(np.float64), A.n)
+
+
+@pytest.mark.parametrize("kind", ["q1_banded", "laplace_permuted"])
+def test_large_share_kernel_neighbour_waits(kind):
+    """CTA shares above 2560 rows with several CTAs: the kernel whose steps end
+    with a wait for the CTAs owning the columns a CTA's rows reach (a banded Q1
+    matrix: the adjacent CTAs; a randomly permuted Laplacian: all of them)."""
+    cg = cg_mod()
+    A = fi.q1(24, 1.0, 64) if kind == "q1_banded" else _permuted(fi.laplace7(20), 65)
+    b = oracle.spmv(A, fi.xstar(64, A.n))
+    with handle(A, ctas=3) as h:
+        max_rows, small = h.partition_info()
+        assert h.nblocks == 3 and max_rows > 2560 and not small
+        res, x = _solve(h, b)
+        res2, x2 = _solve(h, b)  # the flags of the first solve do not leak into the second
+    assert res.status == cg.CG_OK and res.relres <= TOL
+    assert res2.iters == res.iters and np.array_equal(x, x2)
+    ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
+    assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
