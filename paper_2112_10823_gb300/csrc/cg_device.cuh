@@ -504,6 +504,32 @@ __device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U],
 
 #define CGK_SEG_CASES16(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
 
+// The multiply-adds of a lane's first 16 entries (xv holds their gathered
+// values), each followed by the gather of entry 16 + u into the register it
+// frees (N2 = entries of the second batch the step needs, at most 16): the
+// second batch's loads are in flight during the first batch's FMA chain.
+template <typename T, typename X, typename Acc, int N2>
+__device__ __forceinline__ Acc seg_fma_refill_n(const T* vp, const int32_t* cp2, int len, const X* x, X (&xv)[16]) {
+  Acc s = Acc(0);
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    if (u < len) s = fma(Acc(vp[u]), Acc(xv[u]), s);
+    if (u < N2 && 16 + u < len) xv[u] = x[cp2[u]];
+  }
+  return s;
+}
+
+template <typename T, typename X, typename Acc>
+__device__ __forceinline__ Acc seg_fma_refill(const T* vp, const int32_t* cp2, int len, int n2, const X* x,
+                                              X (&xv)[16]) {
+  switch (n2) {
+#define CGK_R(N) case N: return seg_fma_refill_n<T, X, Acc, N>(vp, cp2, len, x, xv);
+    CGK_SEG_CASES16(CGK_R)
+#undef CGK_R
+    default: return Acc(0);
+  }
+}
+
 template <typename X, int U>
 __device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
   static_assert(U == 32 || U == 16, "dispatch covers 1..U");
@@ -695,14 +721,16 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
         const int wmax = (m0 >> kWmaxShift) & 0xff;
         if constexpr (sizeof(X) == 8) {
           // FP64 gathers in batches of 16 (the same FMAs in the same order;
-          // half the registers held by gathered values)
+          // half the registers held by gathered values); the second batch is
+          // loaded during the first batch's FMAs
           X xv[16];
           const int w0 = wmax < 16 ? wmax : 16;
           seg_gather<X, 16>(rc + p0, len, w0, x, xv);
-          part = seg_fma<T, X, Acc, 16>(rv + p0, len, w0, xv, Acc(0));
           if (wmax > 16) {
-            seg_gather<X, 16>(rc + p0 + 16, len - 16, wmax - 16, x, xv);
+            part = seg_fma_refill<T, X, Acc>(rv + p0, rc + p0 + 16, len, wmax - 16, x, xv);
             part = seg_fma<T, X, Acc, 16>(rv + p0 + 16, len - 16, wmax - 16, xv, part);
+          } else {
+            part = seg_fma<T, X, Acc, 16>(rv + p0, len, w0, xv, Acc(0));
           }
         } else {
           X xv[kLaneMax];
