@@ -119,9 +119,11 @@ int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks);
  * The row partition of the persistent kernels: *max_rows = the most rows
  * in one CTA's range; *small_share = 1 if cg_solve runs the small-share
  * kernel on this handle (every range at most 2560 rows: the range's
- * residual kept in shared memory, x updated behind the r.r barrier; the
- * same bits as the other kernel), else 0.  Either pointer may be NULL.
- * Host only: no GPU work.
+ * residual kept in shared memory, x updated behind the r.r barrier), else 0
+ * (the large-share kernel: residual in global memory, x updated with p, and
+ * each step ending with a wait for the CTAs that own the columns of the
+ * CTA's rows only).  Both kernels give the same bits.  Either pointer may be
+ * NULL.  Host only: no GPU work.
  */
 int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* small_share);
 
