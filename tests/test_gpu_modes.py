@@ -110,3 +110,30 @@ def test_large_share_kernel_neighbour_waits(kind):
     assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
     same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
     assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+
+
+@pytest.mark.parametrize("variant", ["mixed", "jacobi", "mixed_jacobi"])
+def test_large_share_kernel_neighbour_waits_variants(variant):
+    """The mixed-precision and Jacobi variants of the large-share kernel (the
+    same neighbour wait) on the permuted Laplacian over three CTAs: the
+    variant's own oracle, and the same bits on a second solve."""
+    cg = cg_mod()
+    A = _permuted(fi.laplace7(20), 66)
+    b = oracle.spmv(A, fi.xstar(66, A.n))
+    mixed = variant.startswith("mixed")
+    jac = variant.endswith("jacobi")
+    opts = {"precision": cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64,
+            "preconditioner": cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE}
+    with handle(A, ctas=3, **opts) as h:
+        assert not h.partition_info()[1]
+        res, x = _solve(h, b)
+        res2, x2 = _solve(h, b)
+    assert res.status == cg.CG_OK and res.relres <= TOL, res
+    assert res2.iters == res.iters and np.array_equal(x, x2)
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1.0000001 * TOL * np.linalg.norm(b)
+    ref = oracle.pcg_jacobi(A, b, tol=TOL, maxit=20 * A.n) if jac else oracle.cg_mixed(A, b, tol=TOL, maxit=20 * A.n)
+    assert ref.status == oracle.OK
+    if not mixed:  # FP64 Jacobi: the oracle's own steps
+        assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    kap = kappa_estimate(A, b)
+    assert np.linalg.norm(x - ref.x) <= 2.02 * kap * TOL * np.linalg.norm(ref.x)
