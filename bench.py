@@ -583,9 +583,13 @@ def run_ours(args):
     flops_launch = solve_flops(n, nnz, iters, mixed, jacobi=jac)
     achieved_gbs = bytes_launch / launch_s / 1e9
     achieved_gflops = flops_launch / launch_s / 1e9
-    side_x = h.partition_info()[1]  # the library's kernel for small CTA shares
-    kname = (f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}, "
-             f"{'true' if side_x else 'false'}>")
+    kernel_kind = h.partition_info()[1]  # the solve kernel the library runs on this system
+    if kernel_kind == cg.CG_SOLVE_KERNEL_CLUSTER:
+        kname = "cg_cluster_kernel"
+    else:
+        small = kernel_kind == cg.CG_SOLVE_KERNEL_SMALL_SHARE
+        kname = (f"cg_solve_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}, "
+                 f"{'true' if small else 'false'}>")
     traffic = recorded_traffic(kname, f"{args.matrix}_{args.grid}")
     if l2_resident(n, nnz, mixed) or not mixed and achieved_gflops / FP64_PEAK_GFLOPS > achieved_gbs / hbm_peak:
         # the system stays in L2 during a solve (or the FP64 pipe is nearer its

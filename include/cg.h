@@ -115,17 +115,26 @@ const char* cg_last_error(cg_handle h);
 /* Matrix size of the handle (n, nnz) and the CTA count of its partition. */
 int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks);
 
+/* The kernel cg_solve runs on a handle (cg_partition_info). */
+enum {
+  CG_SOLVE_KERNEL_LARGE_SHARE = 0, /* whole grid; residual in global memory, x updated with p, each
+                                      step ending with a wait for the CTAs that own the columns of
+                                      the CTA's rows only */
+  CG_SOLVE_KERNEL_SMALL_SHARE = 1, /* whole grid, every CTA range at most 2560 rows: the range's
+                                      residual in shared memory, x updated behind the r.r barrier */
+  CG_SOLVE_KERNEL_CLUSTER = 2      /* plain FP64, at most 16384 rows whose CSR fits the CTAs' shared
+                                      memory, CTA count left automatic: one cluster of 16 CTAs holding
+                                      the system in shared memory */
+};
+
 /*
- * The row partition of the persistent kernels: *max_rows = the most rows
- * in one CTA's range; *small_share = 1 if cg_solve runs the small-share
- * kernel on this handle (every range at most 2560 rows: the range's
- * residual kept in shared memory, x updated behind the r.r barrier), else 0
- * (the large-share kernel: residual in global memory, x updated with p, and
- * each step ending with a wait for the CTAs that own the columns of the
- * CTA's rows only).  Both kernels give the same bits.  Either pointer may be
+ * The partition of the kernel cg_solve runs: *max_rows = the most rows in
+ * one CTA's range; *kernel = one of CG_SOLVE_KERNEL_*.  The two whole-grid
+ * kernels give the same bits; the cluster kernel sums over 16 CTAs instead of
+ * the grid's, so its bits differ within rounding.  Either pointer may be
  * NULL.  Host only: no GPU work.
  */
-int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* small_share);
+int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* kernel);
 
 /*
  * y = A x (Sec. 2.3 / 5.2): y_i = sum_{k=IA(i)}^{IA(i+1)-1} AA(k) x(JA(k)),

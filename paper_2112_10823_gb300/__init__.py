@@ -9,7 +9,8 @@ marshalling only.  Importing it fails if the library is not built.
 """
 from ._binding import (  # noqa: F401
     CG_EBREAKDOWN, CG_EBUSY, CG_ECUDA, CG_EINVAL, CG_ENOMEM, CG_ENOTCONV, CG_ETIMEOUT, CG_OK,
-    CG_PREC_FP64, CG_PREC_MIXED, CG_PRECOND_JACOBI, CG_PRECOND_NONE, LIB_PATH, Batch, BatchResult, CGError, Handle, Request, SolveResult, cg_axpy,
+    CG_PREC_FP64, CG_PREC_MIXED, CG_PRECOND_JACOBI, CG_PRECOND_NONE, CG_SOLVE_KERNEL_CLUSTER,
+    CG_SOLVE_KERNEL_LARGE_SHARE, CG_SOLVE_KERNEL_SMALL_SHARE, LIB_PATH, Batch, BatchResult, CGError, Handle, Request, SolveResult, cg_axpy,
     cg_create,
     cg_destroy, cg_dot, cg_dot_host, cg_dot_noalloc, cg_ewmul, cg_selftest_wait_timeout, cg_solve, cg_spmv, last_error, lib,
 )

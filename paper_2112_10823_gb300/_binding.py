@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "C
                 5: "CG_EBREAKDOWN", 6: "CG_ETIMEOUT", 7: "CG_EBUSY"}
 CG_PREC_FP64, CG_PREC_MIXED = 0, 1
 CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+CG_SOLVE_KERNEL_LARGE_SHARE, CG_SOLVE_KERNEL_SMALL_SHARE, CG_SOLVE_KERNEL_CLUSTER = 0, 1, 2
 
 
 class CGError(RuntimeError):
@@ -197,10 +198,10 @@ class Handle:
         return nb.value
 
     def partition_info(self):
-        """(most rows in one CTA's range, whether cg_solve runs the small-share kernel)."""
-        mr, ss = ctypes.c_int32(0), ctypes.c_int32(0)
-        _check(lib.cg_partition_info(self._h, ctypes.byref(mr), ctypes.byref(ss)), self._h)
-        return mr.value, bool(ss.value)
+        """(most rows in one CTA's range, the CG_SOLVE_KERNEL_* that cg_solve runs)."""
+        mr, kern = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib.cg_partition_info(self._h, ctypes.byref(mr), ctypes.byref(kern)), self._h)
+        return mr.value, kern.value
 
     def close(self):
         if self._h is not None and self._h.value:

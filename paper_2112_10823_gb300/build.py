@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libcg.so")
-UNITS = ["cg_api.cu", "cg_kernels.cu", "batch_kernels.cu", "blas1.cu", "batch.cu"]
+UNITS = ["cg_api.cu", "cg_kernels.cu", "batch_kernels.cu", "blas1.cu", "batch.cu", "cluster_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 f"-I{os.path.join(ROOT, 'include')}"]

@@ -108,6 +108,8 @@ struct cg_ctx {
   int nblocks = 0;
   int nsteps = 0;
   int max_rows = 0;  // most rows in one CTA's range
+  int cluster_R = 0;  // > 0: cg_solve runs the cluster kernel, R rows and E entries per CTA
+  int cluster_E = 0;
   // device memory owned by the handle
   int32_t* d_row_ptr = nullptr;
   int32_t* d_col = nullptr;
@@ -357,6 +359,25 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   h->nsteps = static_cast<int>(part.step.size()) - 2;
   for (int b = 0; b < h->nblocks; ++b)
     h->max_rows = std::max(h->max_rows, part.block_row[b + 1] - part.block_row[b]);
+  // Small plain FP64 systems (the CTA count left automatic): one cluster of
+  // CTAs holding the system in shared memory, if its layout fits and such a
+  // cluster can be resident.
+  if (h->precision == CG_PREC_FP64 && h->preconditioner == CG_PRECOND_NONE && o.ctas <= 0 && n > 0 &&
+      n <= static_cast<int64_t>(cgk::kClusterCtas) * cgk::kClusterMaxRows) {
+    int R = 1;  // rows per CTA: a power of two, so the owner of a column is a shift
+    while (static_cast<int64_t>(R) * cgk::kClusterCtas < n) R <<= 1;
+    int E = 0;
+    for (int c = 0; c < cgk::kClusterCtas; ++c) {
+      const int64_t r0 = std::min<int64_t>(static_cast<int64_t>(c) * R, n);
+      const int64_t r1 = std::min<int64_t>(r0 + R, n);
+      E = std::max(E, rp[r1] - rp[r0]);
+    }
+    E = std::max(E, 1);
+    if (cgk::cluster_max_active(R, E) > 0) {  // 0 if the layout is too large or no cluster fits
+      h->cluster_R = R;
+      h->cluster_E = E;
+    }
+  }
 
   const size_t pad = cgk::kPadEntries;
   CG_TRY(dalloc(h, &h->d_row_ptr, n + 1), "cg_create: cudaMalloc");
@@ -453,10 +474,13 @@ int cg_info(cg_handle h, int64_t* n, int64_t* nnz, int32_t* nblocks) {
   return CG_OK;
 }
 
-int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* small_share) {
+int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* kernel) {
   if (!h) return fail(nullptr, CG_EINVAL, "cg_partition_info: NULL handle");
-  if (max_rows) *max_rows = h->max_rows;
-  if (small_share) *small_share = cgk::small_share(dev_view(h), 0) ? 1 : 0;
+  if (max_rows) *max_rows = h->cluster_R > 0 ? h->cluster_R : h->max_rows;
+  if (kernel)
+    *kernel = h->cluster_R > 0                      ? CG_SOLVE_KERNEL_CLUSTER
+              : cgk::small_share(dev_view(h), 0) ? CG_SOLVE_KERNEL_SMALL_SHARE
+                                                  : CG_SOLVE_KERNEL_LARGE_SHARE;
   return CG_OK;
 }
 
@@ -555,8 +579,12 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   P.chunk_iters = 0;
   P.dinv = h->d_dinv;
   P.flags = h->nblocks > 1 ? h->d_flags : nullptr;
-  e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: cooperative launch");
+  if (h->cluster_R > 0)
+    e = cgk::launch_cluster_solve(h->d_row_ptr, h->d_col, h->d_val, db, dx, h->d_ctrl, tol, maxit,
+                                  static_cast<int32_t>(h->n), h->cluster_R, h->cluster_E, h->stream);
+  else
+    e = cgk::launch_solve(P, h->precision == CG_PREC_MIXED, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: launch");
   e = cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(cgk::SolveCtrl), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cg_solve: read-back");
   if (!x_dev) {

@@ -164,6 +164,19 @@ cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblo
 int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
+
+// Small systems on one thread-block cluster (cluster_solve.cu): kClusterCtas
+// CTAs of kClusterThreads threads, each holding R consecutive rows (R a power
+// of two, at most kClusterMaxRows) and up to E entries in shared memory.
+constexpr int kClusterCtas = 16;  // a non-portable cluster size (opted in)
+constexpr int kClusterThreads = 512;
+constexpr int kClusterMaxRows = 1024;
+size_t cluster_smem_bytes(int R, int E);
+// Clusters of this layout that can be resident at once (0: none, or an error).
+int cluster_max_active(int R, int E);
+cudaError_t launch_cluster_solve(const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                 const double* b, double* x, SolveCtrl* ctrl, double tol, int64_t maxit, int32_t n,
+                                 int32_t R, int32_t E, cudaStream_t s);
 // timeout_site the self-test's wait records
 constexpr int32_t kSelftestSite = 99;
 // timeout_site of a single-system solve's wait for its neighbours' p

@@ -51,11 +51,14 @@ def test_cta_counts(ctas):
         else:
             assert 1 <= h.nblocks
         # one CTA holds all 2744 rows: the kernel with r in global memory;
-        # more CTAs: the small-share kernel (r in shared memory)
-        max_rows, small = h.partition_info()
-        assert max_rows == (A.n if ctas == 1 else max_rows) and max_rows >= -(-A.n // h.nblocks)
-        assert small == (max_rows <= 2560)
-        assert small == (ctas != 1)
+        # 3 or 17 CTAs: the small-share kernel (r in shared memory); the CTA
+        # count left automatic: the cluster kernel (a system this small)
+        max_rows, kernel = h.partition_info()
+        if ctas == 0:
+            assert kernel == cg.CG_SOLVE_KERNEL_CLUSTER and max_rows == 256  # 2744 rows: 16 x 256 >= 2744
+        else:
+            assert max_rows == (A.n if ctas == 1 else max_rows) and max_rows >= -(-A.n // h.nblocks)
+            assert kernel == (cg.CG_SOLVE_KERNEL_LARGE_SHARE if ctas == 1 else cg.CG_SOLVE_KERNEL_SMALL_SHARE)
         res, x = _solve(h, b)
     assert res.status == cg.CG_OK and res.relres <= TOL
     ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
@@ -100,8 +103,8 @@ def test_large_share_kernel_neighbour_waits(kind):
     A = fi.q1(24, 1.0, 64) if kind == "q1_banded" else _permuted(fi.laplace7(20), 65)
     b = oracle.spmv(A, fi.xstar(64, A.n))
     with handle(A, ctas=3) as h:
-        max_rows, small = h.partition_info()
-        assert h.nblocks == 3 and max_rows > 2560 and not small
+        max_rows, kernel = h.partition_info()
+        assert h.nblocks == 3 and max_rows > 2560 and kernel == cg.CG_SOLVE_KERNEL_LARGE_SHARE
         res, x = _solve(h, b)
         res2, x2 = _solve(h, b)  # the flags of the first solve do not leak into the second
     assert res.status == cg.CG_OK and res.relres <= TOL
@@ -125,7 +128,7 @@ def test_large_share_kernel_neighbour_waits_variants(variant):
     opts = {"precision": cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64,
             "preconditioner": cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE}
     with handle(A, ctas=3, **opts) as h:
-        assert not h.partition_info()[1]
+        assert h.partition_info()[1] == cg.CG_SOLVE_KERNEL_LARGE_SHARE
         res, x = _solve(h, b)
         res2, x2 = _solve(h, b)
     assert res.status == cg.CG_OK and res.relres <= TOL, res
@@ -137,3 +140,33 @@ def test_large_share_kernel_neighbour_waits_variants(variant):
         assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
     kap = kappa_estimate(A, b)
     assert np.linalg.norm(x - ref.x) <= 2.02 * kap * TOL * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("kind", ["lap7_16", "q1_16", "rows_fewer_than_ctas", "irregular_long_rows"])
+def test_cluster_kernel(kind):
+    """Small plain FP64 systems with the CTA count left automatic run on one
+    cluster of 16 CTAs holding the system in shared memory: parity with the
+    oracle at equal iterations, the same bits on a second solve; systems with
+    fewer rows than CTAs (empty CTAs) and rows longer than a batch of loads."""
+    cg = cg_mod()
+    if kind == "lap7_16":
+        A = fi.laplace7(16)
+    elif kind == "q1_16":
+        A = fi.q1(16, 1.0, 67)
+    elif kind == "rows_fewer_than_ctas":
+        A = fi.random_spd(5, 68, density=0.6, shift=0.5)
+    else:
+        A = fi.random_spd(300, 69, density=0.3, shift=0.05)
+        assert np.diff(A.row_ptr).max() > 16
+    b = oracle.spmv(A, fi.xstar(67, A.n))
+    with handle(A) as h:
+        assert h.partition_info()[1] == cg.CG_SOLVE_KERNEL_CLUSTER
+        res, x = _solve(h, b)
+        res2, x2 = _solve(h, b)
+    assert res.status == cg.CG_OK and res.relres <= TOL, res
+    assert res2.iters == res.iters and np.array_equal(x, x2)
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1.0000001 * TOL * np.linalg.norm(b)
+    ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
+    assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+    same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
