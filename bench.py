@@ -46,6 +46,7 @@ ITERS_PER_EDGE = 6.2
 SIGMA = 1.0
 TOL = 1e-10
 L2_FLUSH_BYTES = 256 << 20  # > the 126.5 MiB L2
+ENERGY_MIN_S = 1.0  # board energy and latency percentiles over at least this long
 # FP64 FMA peak of one GB300 (152 SMs x ~2 DFMA/clk x 2 flop at 2.07 GHz);
 # measured 600.5 G DFMA/s with an independent-chain probe.
 FP64_PEAK_GFLOPS = 1201.0
@@ -508,7 +509,9 @@ def run_ours(args):
     lat = []
     e0 = energy.read_j()
     tl0 = time.perf_counter()
-    for _ in range(args.latency_solves):
+    # at least latency_solves solves and at least ENERGY_MIN_S seconds of them
+    # (the board energy counter needs a second or so to resolve a small solve)
+    while len(lat) < args.latency_solves or time.perf_counter() - tl0 < ENERGY_MIN_S:
         s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         x.zero_()
         s_ev.record(stream)
@@ -518,7 +521,7 @@ def run_ours(args):
         lat.append(s_ev.elapsed_time(e_ev))
     tl = time.perf_counter() - tl0
     e1 = energy.read_j()
-    joules = (e1 - e0) / args.latency_solves if (e0 is not None and e1 is not None) else None
+    joules = (e1 - e0) / len(lat) if (e0 is not None and e1 is not None) else None
     watts = (e1 - e0) / tl if (e0 is not None and e1 is not None) else None
 
     # ---- BLAS-1 kernels alone (the vector operations of Sec. 5.2): the paper's
@@ -627,10 +630,10 @@ def run_ours(args):
                  "l2": "flushed before every call", "precision": "fp64"},
         "blas1": {k: dict(v, frac=v["gbs"] / hbm_peak) for k, v in blas1.items()},
         "energy": {"joules_per_solve": joules, "avg_watts": watts, "idle_watts": idle_watts,
-                   "joules_per_solve_above_idle": (joules - idle_watts * tl / args.latency_solves
+                   "joules_per_solve_above_idle": (joules - idle_watts * tl / len(lat)
                                                    if joules is not None and idle_watts is not None else None),
                    "source": "NVML board energy",
-                   "solves": args.latency_solves},
+                   "solves": len(lat), "seconds": tl},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "solves": len(lat)},
         "e2e": e2e,
