@@ -11,6 +11,8 @@
  * Every loop runs in index order; there is no blocking, fusion or reordering.
  *
  *   oracle_spmv   CSR product, Sec. 2.3 (the IA/JA/AA definition) and Sec. 5.2
+ *   oracle_spmv_rows  the same product for a list of rows only (single outputs
+ *                 of products too large to redo whole)
  *   oracle_dot    dot product, Sec. 5.2 ("Dot product" table)
  *   oracle_axpy   addition of vectors y <- a x + y, Sec. 5.2 (table labelled daxpy)
  *   oracle_ewmul  element-wise product, Sec. 5.2
@@ -29,7 +31,10 @@
  * the tests under tests/test_oracle_pins.py: the paper's 5x5 CSR example,
  * dense brute force, closed-form eigenpairs of the 7-point and Q1 operators,
  * finite termination, monotone A-norm error, the Chebyshev residual bound,
- * Lanczos extreme eigenvalues and manufactured solutions.
+ * Lanczos extreme eigenvalues and manufactured solutions; for the mixed
+ * iteration also the exact first step on integer data, the replacement
+ * schedule (recursive = true residual to the bit after every replacement) and
+ * FP32-rounding closeness to FP64 CG's early iterates.
  */
 #include <stdint.h>
 #include <math.h>
@@ -176,11 +181,15 @@ void oracle_spmv_f32(int64_t n, const int32_t* IA, const int32_t* JA, const floa
  *   beta >> 1 at that replacement and the iteration stalls along the old
  *   direction: the small Q1 systems never converge that way.)
  *   Convergence needs the true residual: sqrt(rho_true) <= tol*||b||.
+ * If force_iters >= 0, exactly force_iters steps run: the replacements are
+ * made as above (periodic, and whenever the recursive residual reaches
+ * tol*||b||), but reaching the tolerance does not end the iteration, so the
+ * iterate can be compared with a solver that stopped after that many steps.
  * Returns iterations and both residual measures as oracle_cg does.
  */
 int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const double* AA,
                     const float* AA32, int base, const double* b, double* x, double tol,
-                    int64_t maxit, int64_t replace_every, int64_t* iters,
+                    int64_t maxit, int64_t replace_every, int64_t force_iters, int64_t* iters,
                     double* relres_rec, double* relres_true) {
     size_t m = (size_t)(n > 0 ? n : 1);
     double* r = (double*)malloc(sizeof(double) * m);
@@ -202,8 +211,9 @@ int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const doubl
     for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
     double rho = oracle_dot(n, r, r);
     int64_t k = 0;
-    int done = sqrt(rho) <= tol * bnorm;
-    while (!done && k < maxit) {
+    int done = (force_iters < 0) && (sqrt(rho) <= tol * bnorm);
+    int64_t limit = force_iters >= 0 ? force_iters : maxit;
+    while (!done && k < limit) {
         for (int64_t i = 0; i < n; ++i) p32[i] = (float)p[i];
         oracle_spmv_f32(n, IA, JA, AA32, base, p32, q32);
         for (int64_t i = 0; i < n; ++i) q[i] = (double)q32[i];
@@ -220,14 +230,14 @@ int oracle_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const doubl
             oracle_spmv(n, IA, JA, AA, base, x, q);
             for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
             rho_new = oracle_dot(n, r, r);
-            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }
+            if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }
         }
         for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
         rho = rho_new;
     }
     *iters = k;
     *relres_rec = sqrt(rho) / bnorm;
-    if (status == ORC_OK && !done) status = ORC_NOTCONV;
+    if (status == ORC_OK && force_iters < 0 && !done) status = ORC_NOTCONV;
     oracle_spmv(n, IA, JA, AA, base, x, q);
     double t = 0.0;
     for (int64_t i = 0; i < n; ++i) { double d = b[i] - q[i]; t = t + d * d; }

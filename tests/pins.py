@@ -60,6 +60,37 @@ def pin_spmv_dense_bruteforce(seed: int = 3):
         assert np.array_equal(oracle.spmv(Ai, xi), Di @ xi)
 
 
+def pin_spmv_rows():
+    """The row-selected product (Sec. 2.3 definition restricted to listed rows):
+    on the paper's 5x5 example its entries are the printed products' entries
+    for any row list (shuffled, repeated), 1- and 0-based; on irregular 1-based
+    CSR (empty rows, rows longer than 32) with a shuffled row list it equals
+    the dense product's rows, exactly for integer data."""
+    g, A1, A0 = load_paper_example()
+    rows = np.array([4, 0, 2, 2, 3, 1, 4], dtype=np.int64)
+    for p in g["products"]:
+        x = np.array(p["x"], dtype=np.float64)
+        want = np.array(p["Ax"], dtype=np.float64)[rows]
+        assert np.array_equal(oracle.spmv_rows(A1, x, rows), want)
+        assert np.array_equal(oracle.spmv_rows(A0, x, rows), want)
+    assert oracle.spmv_rows(A1, np.ones(5), np.zeros(0, dtype=np.int64)).shape == (0,)
+    for s in (5, 6):
+        A = fi.random_csr(70, s, 0, 12, empty_frac=0.2, long_rows=(45, 70), ncols=70)
+        A.n = 70
+        A1i = fi.to_one_based(A)
+        D = A.to_dense()
+        x = fi.uniform(s, 19, 70)
+        sel = np.random.default_rng(s).permutation(70)[:41].astype(np.int64)
+        ref = (D @ x)[sel]
+        scale = (np.abs(D) @ np.abs(x))[sel]
+        for M in (A, A1i):
+            y = oracle.spmv_rows(M, x, sel)
+            assert np.all(np.abs(y - ref) <= 1e-14 * np.maximum(scale, 1e-300))
+        Ai = fi.random_csr(70, s + 50, 0, 40, empty_frac=0.1, integer=True)
+        xi = np.round(fi.uniform(s, 20, 70, -9, 9))
+        assert np.array_equal(oracle.spmv_rows(fi.to_one_based(Ai), xi, sel), (Ai.to_dense() @ xi)[sel])
+
+
 def laplace7_eigpair(N: int, j: int, k: int, l: int):
     idx = np.arange(1, N + 1)
     th = np.pi / (N + 1)
@@ -247,6 +278,58 @@ def pin_mixed_cg():
         assert r.iters <= 1.5 * r64.iters + 10, (N, r.iters, r64.iters)
 
 
+def pin_mixed_forced_steps():
+    """The mixed iteration run for exactly k steps (force_iters), against facts
+    outside it:
+    (1) one step from x0 = 0 on an integer matrix with an integer right-hand
+        side: the FP32 product of integers below 2^24 is exact, so the step is
+        the textbook first CG step x1 = (b.b / b.Ab) b, to the bit;
+    (2) a residual replacement every `every` steps: after a multiple of
+        `every` steps the recursive residual is the true residual b - A x, to
+        the bit, and in between it is not (the FP32 product drifts it);
+    (3) early iterates stay within FP32 rounding of FP64 CG's iterates for the
+        same step count, far closer than to the neighbouring steps';
+    (4) forcing the converged run's step count reproduces it to the bit, and
+        forcing more steps than convergence needs runs them all."""
+    L = fi.laplace7(5)
+    D = L.to_dense()
+    bi = np.round(fi.uniform(41, 3, L.n, -9, 9))
+    r1 = oracle.cg_mixed(L, bi, tol=0.0, replace_every=50, force_iters=1)
+    bb, bab = int(np.dot(bi.astype(np.int64), bi.astype(np.int64))), int(bi.astype(np.int64) @ (D.astype(np.int64) @ bi.astype(np.int64)))
+    alpha = float(bb) / float(bab)
+    assert r1.iters == 1 and np.array_equal(r1.x, alpha * bi)
+    # (2)
+    A = fi.q1(6, sigma=1.0, seed=43)
+    b = oracle.spmv(A, fi.xstar(43, A.n))
+    every = 4
+    differ = 0
+    for k in range(1, 13):
+        r = oracle.cg_mixed(A, b, tol=1e-30, replace_every=every, force_iters=k)
+        assert r.iters == k
+        if k % every == 0:
+            assert r.relres_rec == r.relres_true, (k, r.relres_rec, r.relres_true)
+        else:
+            differ += r.relres_rec != r.relres_true
+    assert differ >= 6, differ
+    # (3)
+    prev = None
+    for k in range(1, 9):
+        xm = oracle.cg_mixed(A, b, tol=0.0, replace_every=50, force_iters=k).x
+        x64 = oracle.cg(A, b, tol=0.0, maxit=k, force_iters=k).x
+        d = np.linalg.norm(xm - x64)
+        assert d <= 1e-5 * np.linalg.norm(x64), (k, d)
+        if prev is not None:
+            assert np.linalg.norm(x64 - prev) >= 100 * d, k
+        prev = x64
+    # (4)
+    conv = oracle.cg_mixed(A, b, tol=1e-10, replace_every=every)
+    assert conv.status == oracle.OK
+    again = oracle.cg_mixed(A, b, tol=1e-10, replace_every=every, force_iters=conv.iters)
+    assert again.iters == conv.iters and np.array_equal(again.x, conv.x)
+    more = oracle.cg_mixed(A, b, tol=1e-10, replace_every=every, force_iters=conv.iters + 7)
+    assert more.iters == conv.iters + 7 and more.relres_true <= 1e-9
+
+
 def pin_matrix_stats(golden_table1=True):
     """Table 1 column definitions: the 5x5 example by hand and the paper's own
     density and nz/h columns recomputed from its h and nz."""
@@ -323,9 +406,57 @@ def pin_pcg_jacobi():
     assert oracle.pcg_jacobi(Bad, np.ones(2)).status == oracle.BREAKDOWN
 
 
+def pin_omp_variant():
+    """The OpenMP timing variant against the sequential oracle (itself pinned
+    above) and against mathematics: with one thread the same bits for CG and
+    the product; with every host core the product's bits, iterates at equal
+    step counts within 1e-9 relative (the dot products' block order is the
+    only difference), stopping steps within max(2, 1 %); the 7-point
+    Laplacian's Chebyshev step bound; b = 0 and breakdown."""
+    if not oracle.omp_available():
+        import pytest
+        pytest.skip("no OpenMP on this host compiler")
+    cases = [(fi.laplace7(16), 0), (fi.q1(12, 1.0, 1), 1), (fi.q1(20, 1.0, 3), 3)]
+    full = oracle.omp_threads()
+    try:
+        for T in (1, max(full, 3)):
+            oracle.omp_set_threads(T)
+            for A, seed in cases:
+                b = oracle.spmv(A, fi.xstar(seed, A.n))
+                assert np.array_equal(oracle.omp_spmv(A, b), oracle.spmv(A, b))
+                seq = oracle.cg(A, b, tol=1e-10, maxit=10 * A.n)
+                par = oracle.omp_cg(A, b, tol=1e-10, maxit=10 * A.n)
+                assert par.status == oracle.OK and par.relres_true <= 1e-10 * 1.0000001
+                if T == 1:
+                    assert par.iters == seq.iters and np.array_equal(par.x, seq.x)
+                    assert par.relres_true == seq.relres_true
+                    assert oracle.omp_dot(b, b) == oracle.dot(b, b)
+                else:
+                    assert abs(par.iters - seq.iters) <= max(2, math.ceil(0.01 * seq.iters))
+                    same = oracle.cg(A, b, force_iters=par.iters)
+                    assert np.linalg.norm(par.x - same.x) <= 1e-9 * np.linalg.norm(same.x)
+                    exact = math.fsum((b * b).tolist())
+                    assert abs(oracle.omp_dot(b, b) - exact) <= 2 * A.n * 2.0 ** -53 * exact
+        N = 16
+        A = fi.laplace7(N)
+        lmin = 12.0 * math.sin(math.pi / (2 * (N + 1))) ** 2
+        lmax = 12.0 * math.sin(N * math.pi / (2 * (N + 1))) ** 2
+        c = (math.sqrt(lmax / lmin) - 1) / (math.sqrt(lmax / lmin) + 1)
+        kmax = math.ceil(math.log(1e-10 / (2 * math.sqrt(lmax / lmin))) / math.log(c))
+        r = oracle.omp_cg(A, oracle.spmv(A, fi.xstar(0, A.n)), tol=1e-10, maxit=A.n)
+        assert r.status == oracle.OK and r.iters <= kmax
+        z = oracle.omp_cg(A, np.zeros(A.n), x0=np.ones(A.n))
+        assert z.status == oracle.OK and z.iters == 0 and np.all(z.x == 0)
+        Ind = fi.dense_to_csr(np.diag([1.0, -1.0]))
+        assert oracle.omp_cg(Ind, np.array([1.0, 1.0])).status == oracle.BREAKDOWN
+    finally:
+        oracle.omp_set_threads(full)
+
+
 ALL_PINS = [
     pin_spmv_paper_example,
     pin_spmv_dense_bruteforce,
+    pin_spmv_rows,
     pin_laplace7_eigenpairs,
     pin_q1_eigenpairs,
     pin_blas1,
@@ -335,6 +466,8 @@ ALL_PINS = [
     pin_cg_orthogonality,
     pin_cg_special_cases,
     pin_mixed_cg,
+    pin_mixed_forced_steps,
     pin_pcg_jacobi,
     pin_matrix_stats,
+    pin_omp_variant,
 ]

@@ -1,9 +1,8 @@
 """Plant plausible mistakes in copies of the oracle and check that the pins
 catch every one of them (CPU only; the oracle's own source is not touched)."""
 import os
-import shutil
 import subprocess
-import tempfile
+import sys
 
 import pytest
 
@@ -28,17 +27,30 @@ MUTANTS = [
      "for (int64_t i = 0; i < n; ++i) r[i] = r[i] + alpha * q[i];\n        double rho_new = oracle_dot(n, r, r);\n        k = k + 1;\n        if (alpha_h"),
     ("cg_beta_inverted", "double beta = rho_new / rho;\n        if (beta_h",
      "double beta = rho / rho_new;\n        if (beta_h"),
-    ("cg_direction_drops_beta", "for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];\n        rho = rho_new;\n    }\n    *iters = k;\n    *relres_rec = sqrt(rho) / bnorm;\n    if (status == ORC_OK && force_iters",
-     "for (int64_t i = 0; i < n; ++i) p[i] = r[i];\n        rho = rho_new;\n    }\n    *iters = k;\n    *relres_rec = sqrt(rho) / bnorm;\n    if (status == ORC_OK && force_iters"),
+    ("cg_direction_drops_beta",
+     "beta_h[k - 1] = beta;\n        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];",
+     "beta_h[k - 1] = beta;\n        for (int64_t i = 0; i < n; ++i) p[i] = r[i];"),
     ("cg_alpha_uses_old_gamma_sign", "double alpha = rho / gamma;\n        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];\n        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];\n        double rho_new = oracle_dot(n, r, r);\n        k = k + 1;\n        if (alpha_h",
      "double alpha = rho / gamma;\n        for (int64_t i = 0; i < n; ++i) x[i] = x[i] - alpha * p[i];\n        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];\n        double rho_new = oracle_dot(n, r, r);\n        k = k + 1;\n        if (alpha_h"),
-    ("cg_stop_test_squared", "if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm)",
-     "if (force_iters < 0 && rho_new <= tol * bnorm)"),
+    ("cg_stop_test_squared",
+     "if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        double beta",
+     "if (force_iters < 0 && rho_new <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        double beta"),
     ("mixed_never_replaces", "int replace = (replace_every > 0 && k % replace_every == 0) || sqrt(rho_new) <= tol * bnorm;",
      "int replace = 0; if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }"),
     ("mixed_beta_from_true_residual",
-     "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
-     "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n            beta = rho_new / rho;\n        }"),
+     "            if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
+     "            if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n"
+     "            beta = rho_new / rho;\n        }"),
+    ("mixed_forced_run_stops_at_tolerance",
+     "            if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
+     "            if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }"),
+    ("mixed_forced_one_extra_step",
+     "int64_t limit = force_iters >= 0 ? force_iters : maxit;\n    while (!done && k < limit) {\n        for (int64_t i = 0; i < n; ++i) p32[i]",
+     "int64_t limit = force_iters >= 0 ? force_iters + 1 : maxit;\n    while (!done && k < limit) {\n        for (int64_t i = 0; i < n; ++i) p32[i]"),
+    ("mixed_replacement_schedule_offset", "k % replace_every == 0", "k % replace_every == 1"),
+    ("spmv_rows_row_is_list_position", "int64_t i = rows[t];", "int64_t i = t;"),
+    ("spmv_rows_ignores_base", "s = s + AA[k] * x[JA[k] - base];\n        y_sel[t] = s;",
+     "s = s + AA[k] * x[JA[k]];\n        y_sel[t] = s;"),
     ("pcg_no_preconditioner", "oracle_ewmul(n, dinv, r, z);\n        double rho_new = oracle_dot(n, r, z);",
      "for (int64_t i = 0; i < n; ++i) z[i] = r[i];\n        double rho_new = oracle_dot(n, r, z);"),
     ("pcg_rho_uses_r_r", "double rho_new = oracle_dot(n, r, z);", "double rho_new = oracle_dot(n, r, r);"),
@@ -50,10 +62,43 @@ MUTANTS = [
 ]
 
 
+# Mistakes planted in the OpenMP timing variant (cg_oracle_omp.c).
+OMP_SRC = os.path.join(os.path.dirname(oracle.__file__), "cg_oracle_omp.c")
+OMP_MUTANTS = [
+    ("omp_dot_drops_last_block", "for (int t = 0; t < T; ++t) s = s + part[t];",
+     "for (int t = 0; t + 1 < T; ++t) s = s + part[t];"),
+    ("omp_blocks_overlap", "*hi = (n * (t + 1)) / T;", "*hi = (n * (t + 1)) / T + (t + 1 < T);"),
+    ("omp_spmv_drops_last_entry", "k < (int64_t)IA[i + 1] - base; ++k)", "k < (int64_t)IA[i + 1] - base - 1; ++k)"),
+    ("omp_beta_inverted", "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    ("omp_x_update_sign", "x[i] = x[i] + alpha * p[i];", "x[i] = x[i] - alpha * p[i];"),
+    ("omp_true_residual_sign", "q[i] = b[i] - q[i];", "q[i] = b[i] + q[i];"),
+]
+
+
 @pytest.fixture(scope="module")
 def src_text():
     with open(SRC) as f:
         return f.read()
+
+
+# Runs every pin against one compiled mutant and prints the names of the pins
+# that failed.  It runs in a child process: a mutant may also read out of
+# bounds and crash, which counts as caught.
+_CHILD = r"""
+import sys
+sys.path[:0] = [sys.argv[2], sys.argv[3]]
+import oracle, pins
+caught = []
+with oracle.using(sys.argv[1]):
+    for pin in pins.ALL_PINS:
+        try:
+            pin()
+        except (AssertionError, FloatingPointError, ValueError, IndexError, OverflowError):
+            caught.append(pin.__name__)
+print("CAUGHT " + " ".join(caught))
+"""
+
+_CHILD_OMP = _CHILD.replace("oracle.using(sys.argv[1])", "oracle.using_omp(sys.argv[1])")
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
@@ -65,11 +110,34 @@ def test_pins_catch_mutant(name, old, new, src_text, tmp_path):
     so = tmp_path / "libmut.so"
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
                            "-o", str(so), str(c), "-lm"])
-    caught = []
-    with oracle.using(str(so)):
-        for pin in pins.ALL_PINS:
-            try:
-                pin()
-            except (AssertionError, FloatingPointError, ValueError, IndexError, OverflowError) as e:
-                caught.append(pin.__name__)
-    assert caught, f"no pin caught mutant {name}"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", _CHILD, str(so), root, os.path.join(root, "tests")],
+                         capture_output=True, text=True, timeout=600)
+    if res.returncode < 0:  # killed by a signal: the mutant crashed on a pin's input
+        return
+    assert res.returncode == 0, res.stderr[-2000:]
+    line = [ln for ln in res.stdout.splitlines() if ln.startswith("CAUGHT")][-1]
+    assert line.split()[1:], f"no pin caught mutant {name}"
+
+
+@pytest.mark.parametrize("name,old,new", OMP_MUTANTS, ids=[m[0] for m in OMP_MUTANTS])
+def test_pins_catch_omp_mutant(name, old, new, tmp_path):
+    import oracle as orc
+    if not orc.omp_available():
+        pytest.skip("no OpenMP on this host compiler")
+    with open(OMP_SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation site for {name} not unique/found"
+    c = tmp_path / "mut_omp.c"
+    c.write_text(text.replace(old, new))
+    so = tmp_path / "libmut_omp.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-o", str(so), str(c), "-lm"])
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", _CHILD_OMP, str(so), root, os.path.join(root, "tests")],
+                         capture_output=True, text=True, timeout=600)
+    if res.returncode < 0:
+        return
+    assert res.returncode == 0, res.stderr[-2000:]
+    line = [ln for ln in res.stdout.splitlines() if ln.startswith("CAUGHT")][-1]
+    assert "pin_omp_variant" in line.split()[1:], f"the OpenMP pin did not catch mutant {name}"
