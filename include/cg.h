@@ -143,30 +143,63 @@ int cg_partition_info(cg_handle h, int32_t* max_rows, int32_t* kernel);
  */
 int cg_spmv(cg_handle h, const double* x, double* y);
 
-/*
- * *result = sum_i x_i y_i over n elements (Sec. 5.2 "dot product").
- * x, y: device pointers to n doubles; result: device pointer to one double.
- * Deterministic for a given n: same inputs give the same bits.  Uses the
- * handle's device scratch, so calls on one handle must not overlap in time.
- * n may differ from the matrix size.  Asynchronous.
- */
-int cg_dot(cg_handle h, int64_t n, const double* x, const double* y, double* result);
+/* ------------------------------------------------------------------------
+ * The vector operations of Sec. 5.2 ("Vectors operations" and "Dot product"
+ * tables) as stand-alone calls: no handle.  x, y, z and result are device
+ * pointers of the CURRENT CUDA device (cudaSetDevice before the call if
+ * several are in use) and `stream` a cudaStream_t of that device (NULL = the
+ * legacy default stream).  Work is queued on `stream`; the calls return at
+ * once except cg_dot_host.
+ * ---------------------------------------------------------------------- */
 
 /*
- * cg_dot with the sum returned in host memory: the same kernel (the same
- * bits) on the handle's stream, into a device scalar the handle owns; the
- * call then waits for the stream and writes the sum to *result (host
- * memory).  Synchronous; for tests and callers without a device buffer.
+ * *result = sum_i x_i y_i over n elements (Sec. 5.2 "dot product"); result:
+ * device pointer to one double.  When x and y are 16-byte aligned and n is at
+ * least 32768 the sum streams through a bulk-copy ring (one CTA per SM);
+ * otherwise a grid-stride kernel runs.  Deterministic: the same n and
+ * alignment of x and y give the same bits.
+ * Scratch: the first call on a (device, stream) pair allocates about 8 KB of
+ * device memory (cudaMalloc, so make that first call outside any stream
+ * capture), which later calls on the same pair reuse and cg_blas_release()
+ * frees.  Calls on one stream run in order, so they may share it; calls on
+ * different streams get different scratch.  If a device-side wait of the
+ * kernel gives up (only a fault of the copy engine could cause it), *result
+ * is NaN; cg_dot_host reports it as CG_ETIMEOUT.
  */
-int cg_dot_host(cg_handle h, int64_t n, const double* x, const double* y, double* result);
+int cg_dot(int64_t n, const double* x, const double* y, double* result, void* stream);
 
-/* y <- a x + y over n elements (Sec. 5.2 "addition of vectors"), FMA.
- * Device pointers; x and y must not overlap.  Asynchronous. */
-int cg_axpy(cg_handle h, int64_t n, double a, const double* x, double* y);
+/*
+ * cg_dot with the sum written to *result in host memory: the same kernel (the
+ * same bits) into the scratch's device scalar, then a copy to the host and a
+ * synchronisation of `stream`.  Synchronous; for tests and callers without a
+ * device buffer.
+ */
+int cg_dot_host(int64_t n, const double* x, const double* y, double* result, void* stream);
 
-/* z_i = x_i * y_i over n elements (Sec. 5.2 "element wise product").
- * Device pointers; z may alias x or y exactly.  Asynchronous. */
-int cg_ewmul(cg_handle h, int64_t n, const double* x, const double* y, double* z);
+/* y <- a x + y over n elements (Sec. 5.2 "addition of vectors"), one FMA per
+ * element.  x and y must not overlap.  16-byte accesses when both are
+ * 16-byte aligned.  No scratch. */
+int cg_axpy(int64_t n, double a, const double* x, double* y, void* stream);
+
+/* z_i = x_i * y_i over n elements (Sec. 5.2 "element wise product"); z may
+ * alias x or y exactly.  No scratch. */
+int cg_ewmul(int64_t n, const double* x, const double* y, double* z, void* stream);
+
+/* Free the dot product's scratch of every (device, stream) pair.  No call of
+ * cg_dot / cg_dot_host may be queued or running on any of them.  Later calls
+ * allocate again. */
+int cg_blas_release(void);
+
+/*
+ * FP64 fused multiply-add throughput of `device` (-1 = the current device)
+ * in GFLOP/s (2 flops per FMA): a kernel of 2, 4 and 8 CTAs of 256 threads
+ * per SM, each thread running eight independent FMA chains, timed with CUDA
+ * events over about 40 ms per launch (the best of three timed launches after
+ * two warm-up launches, for each CTA count).  The ceiling of the ALU roofline that the CG solves of systems
+ * resident in L2 are held against; no counterpart in the paper, which
+ * reports times only.  Synchronous; allocates and frees a small buffer.
+ */
+int cg_probe_fp64_peak(int32_t device, double* gflops);
 
 /*
  * Solve A x = b by classical CG (Sec. 5.3; Hestenes-Stiefel form):
@@ -191,24 +224,29 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
              double* relres);
 
 /*
- * *result = sum_i x_i y_i over n elements, like cg_dot, but without a handle
- * and without allocating anything.  The paper has no counterpart: this entry
+ * *result = sum_i x_i y_i over n elements, like cg_dot, but without
+ * allocating anything.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate GPU memory at the moment they
  * need a dot product, for example code running under a fixed memory budget
  * that forbids allocation after start-up, code called from inside another
  * allocator or memory pool that must not be re-entered, or latency-critical
  * loops that cannot afford cudaMalloc's implicit device synchronisation.
- * (cg_create, which cg_dot needs, allocates device memory.)
+ * (cg_dot allocates its scratch on the first call for each stream.)
  *
- * x, y: device pointers to n doubles; result: device pointer to one double;
- * stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * x, y: device pointers to n doubles and result a device pointer to one
+ * double, all of the CURRENT CUDA device, and stream a cudaStream_t of that
+ * device (NULL = legacy default stream): the call finds the array's address
+ * on the current device, so memory or a stream of another device would be
+ * paired with the wrong array.  Asynchronous.
  * The scratch (per-CTA partial sums and an arrival counter) is one fixed
  * array of about 128 KB compiled into the library, so n is limited to
  * 33,554,432 elements (CG_EINVAL beyond, with a message).  Every GPU that
  * loads the library holds that array until the process exits.
  * The first call on each device looks up the array's device address (a CUDA
  * runtime call made with that device current); make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on
+ * any stream capture.  The cached address belongs to the device's current
+ * context: after cudaDeviceReset the array must not be used again in that
+ * process.  All calls share the one array: calls that overlap on
  * the GPU (different streams, or different host threads) race and give wrong
  * results; serialise them.  Each call clears the counter it needs before its
  * kernel runs.  Deterministic for a given n.

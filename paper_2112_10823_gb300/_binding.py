@@ -95,13 +95,17 @@ def _load() -> ctypes.CDLL:
     lib.cg_spmv.restype = ctypes.c_int
     lib.cg_spmv.argtypes = [vp, vp, vp]
     lib.cg_dot.restype = ctypes.c_int
-    lib.cg_dot.argtypes = [vp, i64, vp, vp, vp]
+    lib.cg_dot.argtypes = [i64, vp, vp, vp, vp]
     lib.cg_dot_host.restype = ctypes.c_int
-    lib.cg_dot_host.argtypes = [vp, i64, vp, vp, P(ctypes.c_double)]
+    lib.cg_dot_host.argtypes = [i64, vp, vp, P(ctypes.c_double), vp]
     lib.cg_axpy.restype = ctypes.c_int
-    lib.cg_axpy.argtypes = [vp, i64, dbl, vp, vp]
+    lib.cg_axpy.argtypes = [i64, dbl, vp, vp, vp]
     lib.cg_ewmul.restype = ctypes.c_int
-    lib.cg_ewmul.argtypes = [vp, i64, vp, vp, vp]
+    lib.cg_ewmul.argtypes = [i64, vp, vp, vp, vp]
+    lib.cg_blas_release.restype = ctypes.c_int
+    lib.cg_blas_release.argtypes = []
+    lib.cg_probe_fp64_peak.restype = ctypes.c_int
+    lib.cg_probe_fp64_peak.argtypes = [i32, P(dbl)]
     lib.cg_solve.restype = ctypes.c_int
     lib.cg_solve.argtypes = [vp, vp, vp, dbl, i64, P(i64), P(dbl)]
     lib.cg_dot_noalloc.restype = ctypes.c_int
@@ -279,53 +283,84 @@ def cg_spmv(h: Handle, x, y) -> None:
     _check(lib.cg_spmv(h._h, _ptr(x), _ptr(y)), h._h)
 
 
-def cg_dot(h: Handle, x, y, out, n: int | None = None) -> None:
-    """out[0] = x . y (CUDA float64 tensors; out has at least one element)."""
-    n = x.numel() if n is None else int(n)
-    _check_f64("x", x, n)
-    _check_f64("y", y, n)
-    _check_f64("out", out, 1)
-    _check(lib.cg_dot(h._h, n, _ptr(x), _ptr(y), _ptr(out)), h._h)
+def _stream_of(t, stream) -> int:
+    """Raw cudaStream_t: the given torch stream or int, else torch's current
+    stream on the tensor's device."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def cg_dot_host(h: Handle, x, y, n: int | None = None) -> float:
-    """x . y (CUDA float64 tensors) returned to the host; synchronous."""
-    n = x.numel() if n is None else int(n)
-    _check_f64("x", x, n)
-    _check_f64("y", y, n)
-    r = ctypes.c_double(float("nan"))
-    _check(lib.cg_dot_host(h._h, n, _ptr(x), _ptr(y), ctypes.byref(r)), h._h)
-    return r.value
-
-
-def cg_dot_noalloc(x, y, out, n: int | None = None, stream=None) -> None:
-    """out[0] = x . y without a handle and without any allocation (fixed
-    library scratch; n <= 33,554,432; concurrent calls race)."""
+def cg_dot(x, y, out, n: int | None = None, stream=None) -> None:
+    """out[0] = x . y (CUDA float64 tensors of one device; out has at least one
+    element).  Runs on ``stream`` (default: torch's current stream)."""
     import torch
     n = x.numel() if n is None else int(n)
     _check_f64("x", x, n)
     _check_f64("y", y, n)
     _check_f64("out", out, 1)
-    if stream is None:
-        stream = torch.cuda.current_stream(out.device)
-    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    _check(lib.cg_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(out), s))
+    with torch.cuda.device(x.device):
+        _check(lib.cg_dot(n, _ptr(x), _ptr(y), _ptr(out), _stream_of(x, stream)))
 
 
-def cg_axpy(h: Handle, a: float, x, y, n: int | None = None) -> None:
-    """y <- a x + y."""
+def cg_dot_host(x, y, n: int | None = None, stream=None) -> float:
+    """x . y (CUDA float64 tensors) returned to the host; synchronous."""
+    import torch
     n = x.numel() if n is None else int(n)
     _check_f64("x", x, n)
     _check_f64("y", y, n)
-    _check(lib.cg_axpy(h._h, n, float(a), _ptr(x), _ptr(y)), h._h)
+    r = ctypes.c_double(float("nan"))
+    with torch.cuda.device(x.device):
+        _check(lib.cg_dot_host(n, _ptr(x), _ptr(y), ctypes.byref(r), _stream_of(x, stream)))
+    return r.value
 
 
-def cg_ewmul(h: Handle, x, y, z, n: int | None = None) -> None:
+def cg_dot_noalloc(x, y, out, n: int | None = None, stream=None) -> None:
+    """out[0] = x . y without any allocation (fixed library scratch;
+    n <= 33,554,432; concurrent calls race).  The call runs with the tensors'
+    device current, which the library's lookup of its scratch relies on."""
+    import torch
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    _check_f64("out", out, 1)
+    if x.device != out.device or y.device != out.device:
+        raise ValueError("x, y and out must be on one device")
+    with torch.cuda.device(out.device):
+        _check(lib.cg_dot_noalloc(n, _ptr(x), _ptr(y), _ptr(out), _stream_of(out, stream)))
+
+
+def cg_axpy(a: float, x, y, n: int | None = None, stream=None) -> None:
+    """y <- a x + y."""
+    import torch
+    n = x.numel() if n is None else int(n)
+    _check_f64("x", x, n)
+    _check_f64("y", y, n)
+    with torch.cuda.device(x.device):
+        _check(lib.cg_axpy(n, float(a), _ptr(x), _ptr(y), _stream_of(x, stream)))
+
+
+def cg_ewmul(x, y, z, n: int | None = None, stream=None) -> None:
     """z = x * y element-wise."""
+    import torch
     n = x.numel() if n is None else int(n)
     for nm, t in (("x", x), ("y", y), ("z", z)):
         _check_f64(nm, t, n)
-    _check(lib.cg_ewmul(h._h, n, _ptr(x), _ptr(y), _ptr(z)), h._h)
+    with torch.cuda.device(x.device):
+        _check(lib.cg_ewmul(n, _ptr(x), _ptr(y), _ptr(z), _stream_of(x, stream)))
+
+
+def cg_blas_release() -> None:
+    """Free the dot product's per-stream scratch (no dot call may be in flight)."""
+    _check(lib.cg_blas_release())
+
+
+def cg_probe_fp64_peak(device: int = -1) -> float:
+    """Measured FP64 FMA throughput of the device, GFLOP/s."""
+    g = ctypes.c_double(0.0)
+    _check(lib.cg_probe_fp64_peak(int(device), ctypes.byref(g)))
+    return g.value
 
 
 def cg_solve(h: Handle, b, x, tol: float = 1e-10, maxit: int | None = None, raise_on_error: bool = False

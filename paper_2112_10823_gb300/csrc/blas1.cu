@@ -65,6 +65,171 @@ cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* out,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Streamed dot product: the kernel of cg_dot when x and y are 16-byte aligned
+// and long enough.  One CTA per SM.  A producer warp copies chunks of x and y
+// (kDotChunk elements each) into a ring of kDotSlots shared-memory slots with
+// 1-D bulk copies, completion counted on each slot's "full" mbarrier; eight
+// consumer warps read a slot with 16-byte shared loads, run one FMA per
+// element into eight per-thread accumulators, and release the slot on its
+// "empty" mbarrier.  The copy engine keeps up to kDotSlots * 32 KB in flight
+// per SM whatever the consumers are doing, so the FP64 pipe (one FMA per 16
+// bytes streamed: about two thirds of its peak at the HBM rate) and the
+// memory stream overlap.  Chunk c goes to CTA c mod G; the elements past the
+// last whole chunk to the last CTA.  Every thread sums its accumulators in a
+// fixed order, the CTA in a fixed tree, the last CTA to finish the CTA sums in
+// CTA order: the same bits for a given n.
+constexpr int kDotWarps = 8;
+constexpr int kDotThreads = (kDotWarps + 1) * 32;
+constexpr int kDotChunk = 2048;
+constexpr int kDotSlots = 4;
+constexpr int kDotPerThread = kDotChunk / (kDotWarps * 32);  // 8 elements per slot and thread
+static_assert(kDotPerThread == 8, "the consumer loop reads four double2 of x and of y per slot");
+constexpr size_t kDotSmem = 2 * sizeof(double) * kDotChunk * kDotSlots + 16 * kDotSlots + 16;
+
+int64_t dot_stream_min_n() { return static_cast<int64_t>(kDotChunk) * 16; }
+
+__global__ void __launch_bounds__(kDotThreads, 1)
+    dot_stream_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ out,
+                      double* __restrict__ partials, unsigned int* counter, int32_t* err,
+                      unsigned long long limit_ns) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  double* xs = reinterpret_cast<double*>(dsm);
+  double* ys = xs + kDotChunk * kDotSlots;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ys + kDotChunk * kDotSlots);
+  uint64_t* empty = full + kDotSlots;
+  int32_t* stop = reinterpret_cast<int32_t*>(empty + kDotSlots);
+  __shared__ double red[kDotThreads + 1];
+  __shared__ unsigned int is_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  const int64_t nchunks = n / kDotChunk;
+  const uint32_t mine = nchunks > blockIdx.x ? static_cast<uint32_t>((nchunks - 1 - blockIdx.x) / G + 1) : 0u;
+  if (threadIdx.x < kDotSlots) {
+    mbar_init(&full[threadIdx.x], 1);
+    mbar_init(&empty[threadIdx.x], kDotWarps);
+  }
+  if (threadIdx.x == 0) *stop = 0;
+  if (threadIdx.x < kDotSlots) fence_mbar_init();
+  __syncthreads();
+  double acc = 0.0;
+  if (warp == kDotWarps) {
+    if (lane == 0) {
+      constexpr uint32_t kBytes = kDotChunk * sizeof(double);
+      uint32_t g = 0;
+      for (; g < mine; ++g) {
+        const int s = static_cast<int>(g % kDotSlots);
+        if (g >= kDotSlots && !mbar_wait_bounded(&empty[s], ((g / kDotSlots) - 1) & 1u, limit_ns, stop)) break;
+        const int64_t c = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(g) * G;
+        mbar_arrive_expect_tx(&full[s], 2 * kBytes);
+        bulk_g2s(xs + s * kDotChunk, x + c * kDotChunk, kBytes, &full[s]);
+        bulk_g2s(ys + s * kDotChunk, y + c * kDotChunk, kBytes, &full[s]);
+      }
+      // copies still in flight land before the CTA leaves
+      for (uint32_t k = g > kDotSlots ? g - kDotSlots : 0; k < g; ++k)
+        mbar_wait_bounded(&full[k % kDotSlots], (k / kDotSlots) & 1u, limit_ns, nullptr);
+    }
+  } else {
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (uint32_t g = 0; g < mine; ++g) {
+      const int s = static_cast<int>(g % kDotSlots);
+      if (!mbar_wait_bounded(&full[s], (g / kDotSlots) & 1u, limit_ns, stop)) {
+        atomicExch(stop, 1);
+        break;
+      }
+      const double2* xv = reinterpret_cast<const double2*>(xs + s * kDotChunk);
+      const double2* yv = reinterpret_cast<const double2*>(ys + s * kDotChunk);
+      double2 u[4], v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        u[j] = xv[threadIdx.x + kDotWarps * 32 * j];
+        v[j] = yv[threadIdx.x + kDotWarps * 32 * j];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        a[2 * j] = fma(u[j].x, v[j].x, a[2 * j]);
+        a[2 * j + 1] = fma(u[j].y, v[j].y, a[2 * j + 1]);
+      }
+    }
+    if (blockIdx.x == G - 1)
+      for (int64_t i = nchunks * kDotChunk + threadIdx.x; i < n; i += kDotWarps * 32) a[0] = fma(x[i], y[i], a[0]);
+    acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  }
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    if (ld_volatile_i32(stop)) atomicExch(err, 1);
+    partials[blockIdx.x] = s;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    double t = 0.0;
+    for (int j = threadIdx.x; j < static_cast<int>(gridDim.x); j += kDotThreads) t += __ldcg(partials + j);
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) {
+      // err[0]: raised by any CTA of this call; err[1]: the outcome of the
+      // last call (read by the host after a synchronising call).  Both
+      // words are left ready for the next call, like the counter.
+      const int32_t bad = __ldcg(err);
+      err[1] = bad;
+      err[0] = 0;
+      *out = bad ? __longlong_as_double(0x7ff8000000000000ll) : t;
+      *counter = 0u;
+    }
+  }
+}
+
+cudaError_t launch_dot_stream(int64_t n, const double* x, const double* y, double* out, double* partials,
+                              unsigned int* counter, int32_t* err, int grid, unsigned long long limit_ns,
+                              cudaStream_t s) {
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(dot_stream_kernel), kDotSmem);
+  if (e != cudaSuccess) return e;
+  dot_stream_kernel<<<grid, kDotThreads, kDotSmem, s>>>(n, x, y, out, partials, counter, err, limit_ns);
+  return cudaGetLastError();
+}
+
+// Grid of the streamed dot product: one CTA per SM, fewer if there are fewer
+// whole chunks.
+int dot_stream_grid(int64_t n, int num_sms) {
+  const int64_t nchunks = n / kDotChunk;
+  int64_t g = nchunks < num_sms ? nchunks : num_sms;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 multiply-add throughput probe (the ceiling of the ALU roofline): every
+// thread runs eight independent FMA chains a = a * m + c, whose fixed point is
+// c / (1 - m) = 1, so the values stay finite; the sum is stored only if it
+// takes a value it cannot take, which keeps the compiler from dropping the
+// work without writing anything.
+__global__ void __launch_bounds__(256) fp64_probe_kernel(int64_t iters, double m, double c, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 0.5 + 1e-3 * k + 1e-9 * threadIdx.x;
+  // 32 FMAs per trip of the loop, so its counter and branch are a small
+  // share of the issued instructions
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    }
+  }
+  const double t = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  if (t == -1.0) sink[blockIdx.x] = t;
+}
+
+
+cudaError_t launch_fp64_probe(int64_t iters, int grid, double* sink, cudaStream_t s) {
+  fp64_probe_kernel<<<grid, 256, 0, s>>>(iters, 1.0 - 1.0 / 1024.0, 1.0 / 1024.0, sink);
+  return cudaGetLastError();
+}
+
 namespace {
 inline int stream_grid(int64_t n) {
   int dev = 0, sms = 148;

@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cg.h"
@@ -129,9 +132,6 @@ struct cg_ctx {
   double* d_partials = nullptr;
   cgk::SolveCtrl* d_ctrl = nullptr;  // followed by the CTAs' epoch flags (one allocation, one memset per solve)
   unsigned long long* d_flags = nullptr;
-  double* d_dot_partials = nullptr;
-  unsigned int* d_dot_counter = nullptr;
-  double* d_dot_result = nullptr;  // cg_dot_host's device scalar
   int32_t* d_err = nullptr;
   cgk::SolveCtrl* h_ctrl = nullptr;  // pinned
   std::vector<void*> allocs;
@@ -220,6 +220,90 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+}  // namespace
+
+// ---- BLAS-1 without a handle (Sec. 5.2): scratch per (device, stream)
+
+namespace {
+
+// Scratch of the dot product for one (device, stream) pair, allocated by the
+// first call on that pair: kBlasPartials CTA sums, then the arrival counter
+// and the two error words, then the device scalar of cg_dot_host.  Calls on
+// one stream run one after another, so they can share it; calls on
+// different streams use different scratch.
+constexpr int kBlasPartials = 1024;
+constexpr size_t kBlasScratchBytes = sizeof(double) * (kBlasPartials + 4);
+struct BlasScratch {
+  double* partials;
+  unsigned int* counter;
+  int32_t* err;  // [0] raised by the kernel, [1] outcome of the last call
+  double* result;
+};
+std::mutex g_blas_mu;
+std::map<std::pair<int, uintptr_t>, double*> g_blas;
+
+int sm_count(int dev) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  if (dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev] && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    cache[dev] = 0;
+  }
+  return cache[dev];
+}
+
+cudaError_t blas_scratch(cudaStream_t s, int* dev_out, BlasScratch* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_blas_mu);
+  auto key = std::make_pair(dev, reinterpret_cast<uintptr_t>(s));
+  auto it = g_blas.find(key);
+  double* base = nullptr;
+  if (it == g_blas.end()) {
+    e = cudaMalloc(&base, kBlasScratchBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(base, 0, kBlasScratchBytes, s);
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      return e;
+    }
+    g_blas.emplace(key, base);
+  } else {
+    base = it->second;
+  }
+  out->partials = base;
+  out->counter = reinterpret_cast<unsigned int*>(base + kBlasPartials);
+  out->err = reinterpret_cast<int32_t*>(base + kBlasPartials + 1);
+  out->result = base + kBlasPartials + 2;
+  *dev_out = dev;
+  return cudaSuccess;
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// The dot product into `result` (device; NULL: the scratch's scalar);
+// *streamed tells which kernel ran.
+int dot_launch(const char* who, int64_t n, const double* x, const double* y, double* result, cudaStream_t s,
+               BlasScratch* sc, bool* streamed) {
+  int dev = 0;
+  cudaError_t e = blas_scratch(s, &dev, sc);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, (std::string(who) + ": scratch").c_str());
+  const int sms = sm_count(dev);
+  if (sms <= 0 || 4 * sms > kBlasPartials)
+    return fail(nullptr, CG_ECUDA, std::string(who) + ": unsupported SM count");
+  if (!result) result = sc->result;
+  *streamed = n >= cgk::dot_stream_min_n() && aligned16(x) && aligned16(y);
+  if (*streamed)
+    e = cgk::launch_dot_stream(n, x, y, result, sc->partials, sc->counter, sc->err, cgk::dot_stream_grid(n, sms),
+                               2000000000ull, s);
+  else
+    e = cgk::launch_dot(n, x, y, result, sc->partials, sc->counter, cgk::dot_grid(n, sms), s);
+  return e == cudaSuccess ? CG_OK : cuda_fail(nullptr, e, (std::string(who) + ": launch").c_str());
+}
 
 }  // namespace
 
@@ -399,9 +483,6 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
     h->d_ctrl = reinterpret_cast<cgk::SolveCtrl*>(blk);
     h->d_flags = reinterpret_cast<unsigned long long*>(blk + ctrl_flags_offset());
   }
-  CG_TRY(dalloc(h, &h->d_dot_partials, static_cast<size_t>(4) * sms + 8), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_dot_counter, 4), "cg_create: cudaMalloc");
-  CG_TRY(dalloc(h, &h->d_dot_result, 1), "cg_create: cudaMalloc");
   CG_TRY(dalloc(h, &h->d_err, 4), "cg_create: cudaMalloc");
   if (o.precision == CG_PREC_MIXED) {
     CG_TRY(dalloc(h, &h->d_val32, nnz + pad), "cg_create: cudaMalloc");
@@ -434,7 +515,6 @@ int cg_create(cg_handle* out, const cg_csr* csr, int64_t n, int64_t nnz, const c
   CG_TRY(cudaMemcpy(h->d_block_row, part.block_row.data(), sizeof(int32_t) * part.block_row.size(),
                     cudaMemcpyHostToDevice),
          "cg_create: upload");
-  CG_TRY(cudaMemset(h->d_dot_counter, 0, 16), "cg_create: memset");
   CG_TRY(cudaMemset(h->d_err, 0, 16), "cg_create: memset");
   if (o.precision == CG_PREC_MIXED) {
     CG_TRY(cudaMemset(h->d_val32, 0, sizeof(float) * (nnz + pad)), "cg_create: memset");
@@ -493,44 +573,96 @@ int cg_spmv(cg_handle h, const double* x, double* y) {
   return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_spmv: launch");
 }
 
-int cg_dot(cg_handle h, int64_t n, const double* x, const double* y, double* result) {
-  if (!h) return fail(nullptr, CG_EINVAL, "cg_dot: NULL handle");
-  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_dot: bad arguments");
-  DeviceGuard g(h->device);
-  const int grid = cgk::dot_grid(n, h->num_sms);
-  cudaError_t e = cgk::launch_dot(n, x, y, result, h->d_dot_partials, h->d_dot_counter, grid, h->stream);
-  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_dot: launch");
+int cg_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(nullptr, CG_EINVAL, "cg_dot: bad arguments");
+  BlasScratch sc;
+  bool streamed = false;
+  return dot_launch("cg_dot", n, x, y, result, static_cast<cudaStream_t>(stream), &sc, &streamed);
 }
 
-int cg_dot_host(cg_handle h, int64_t n, const double* x, const double* y, double* result) {
-  if (!h) return fail(nullptr, CG_EINVAL, "cg_dot_host: NULL handle");
-  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_dot_host: bad arguments");
-  DeviceGuard g(h->device);
-  const int grid = cgk::dot_grid(n, h->num_sms);
-  cudaError_t e =
-      cgk::launch_dot(n, x, y, h->d_dot_result, h->d_dot_partials, h->d_dot_counter, grid, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(result, h->d_dot_result, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_dot_host");
+int cg_dot_host(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  if (n < 0 || !result || (n > 0 && (!x || !y))) return fail(nullptr, CG_EINVAL, "cg_dot_host: bad arguments");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BlasScratch sc;
+  bool streamed = false;
+  const int rc = dot_launch("cg_dot_host", n, x, y, nullptr, s, &sc, &streamed);
+  if (rc != CG_OK) return rc;
+  double v = 0.0;
+  int32_t bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, sc.result, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && streamed) e = cudaMemcpyAsync(&bad, sc.err + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_dot_host");
+  if (bad) return fail(nullptr, CG_ETIMEOUT, "cg_dot_host: a device-side wait of the dot kernel gave up");
+  *result = v;
+  return CG_OK;
 }
 
-int cg_axpy(cg_handle h, int64_t n, double a, const double* x, double* y) {
-  if (!h) return fail(nullptr, CG_EINVAL, "cg_axpy: NULL handle");
-  if (n < 0 || (n > 0 && (!x || !y))) return fail(h, CG_EINVAL, "cg_axpy: bad arguments");
+int cg_axpy(int64_t n, double a, const double* x, double* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(nullptr, CG_EINVAL, "cg_axpy: bad arguments");
   if (n == 0) return CG_OK;
-  DeviceGuard g(h->device);
-  cudaError_t e = cgk::launch_axpy(n, a, x, y, h->stream);
-  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_axpy: launch");
+  cudaError_t e = cgk::launch_axpy(n, a, x, y, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CG_OK : cuda_fail(nullptr, e, "cg_axpy: launch");
 }
 
-int cg_ewmul(cg_handle h, int64_t n, const double* x, const double* y, double* z) {
-  if (!h) return fail(nullptr, CG_EINVAL, "cg_ewmul: NULL handle");
-  if (n < 0 || (n > 0 && (!x || !y || !z))) return fail(h, CG_EINVAL, "cg_ewmul: bad arguments");
+int cg_ewmul(int64_t n, const double* x, const double* y, double* z, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y || !z))) return fail(nullptr, CG_EINVAL, "cg_ewmul: bad arguments");
   if (n == 0) return CG_OK;
-  DeviceGuard g(h->device);
-  cudaError_t e = cgk::launch_ewmul(n, x, y, z, h->stream);
-  return e == cudaSuccess ? CG_OK : cuda_fail(h, e, "cg_ewmul: launch");
+  cudaError_t e = cgk::launch_ewmul(n, x, y, z, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CG_OK : cuda_fail(nullptr, e, "cg_ewmul: launch");
+}
+
+int cg_probe_fp64_peak(int32_t device, double* gflops) {
+  if (!gflops) return fail(nullptr, CG_EINVAL, "cg_probe_fp64_peak: NULL output");
+  *gflops = 0.0;
+  int dev = device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, CG_ECUDA, "cg_probe_fp64_peak: no device");
+  DeviceGuard g(dev);
+  const int sms = sm_count(dev);
+  if (sms <= 0) return fail(nullptr, CG_ECUDA, "cg_probe_fp64_peak: SM count");
+  double* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&sink, sizeof(double) * static_cast<size_t>(sms) * 8);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 0.0;
+  // two, four and eight CTAs of 256 threads per SM; for each, two launches
+  // warm up and size the next three to about 40 ms, the best of which counts
+  for (int per_sm = 2; e == cudaSuccess && per_sm <= 8; per_sm *= 2) {
+    const int grid = sms * per_sm;
+    const double per_iter = static_cast<double>(grid) * cgk::kFp64ProbeThreads * cgk::kFp64ProbeFmasPerIter;
+    int64_t iters = 500;
+    for (int rep = 0; e == cudaSuccess && rep < 5; ++rep) {
+      e = cudaEventRecord(e0, nullptr);
+      if (e == cudaSuccess) e = cgk::launch_fp64_probe(iters, grid, sink, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess || ms <= 0.f) break;
+      if (rep >= 2) best = std::max(best, 2.0 * per_iter * static_cast<double>(iters) / (ms * 1e-3) / 1e9);
+      if (rep == 1) iters = std::max<int64_t>(iters, static_cast<int64_t>(iters * (40.0 / ms)));
+    }
+  }
+  if (e1) cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (sink) cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_probe_fp64_peak");
+  *gflops = best;
+  return CG_OK;
+}
+
+int cg_blas_release(void) {
+  std::lock_guard<std::mutex> lock(g_blas_mu);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_blas) {
+    cudaSetDevice(kv.first.first);
+    cudaFree(kv.second);
+  }
+  g_blas.clear();
+  if (cur >= 0) cudaSetDevice(cur);
+  return CG_OK;
 }
 
 int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit, int64_t* iters, double* relres) {

@@ -163,6 +163,20 @@ int solve_blocks_per_sm(bool mixed, bool jacobi);   // occupancy of the persiste
 cudaError_t launch_batch(const BatchParams& B, bool mixed, bool jacobi, int nblocks, cudaStream_t s);
 int batch_blocks_per_sm(bool mixed, bool jacobi);
 int dot_grid(int64_t n, int num_sms);
+// Streamed dot product (x and y 16-byte aligned, n >= dot_stream_min_n()):
+// `grid` = dot_stream_grid(n, SMs) CTAs; err[0] is raised by a wait that gave
+// up, and the last CTA moves it to err[1] (the result is then NaN) and clears
+// it.
+cudaError_t launch_dot_stream(int64_t n, const double* x, const double* y, double* out, double* partials,
+                              unsigned int* counter, int32_t* err, int grid, unsigned long long limit_ns,
+                              cudaStream_t s);
+int dot_stream_grid(int64_t n, int num_sms);
+int64_t dot_stream_min_n();
+// FP64 FMA throughput probe: `grid` CTAs of 256 threads, each thread 8
+// independent chains of 4 x iters FMAs.
+constexpr int kFp64ProbeThreads = 256;
+constexpr int kFp64ProbeFmasPerIter = 32;
+cudaError_t launch_fp64_probe(int64_t iters, int grid, double* sink, cudaStream_t s);
 cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long limit_ns, cudaStream_t s);
 
 // Small systems on one thread-block cluster (cluster_solve.cu): kClusterCtas

@@ -132,4 +132,10 @@ def test_null_handle_queries_rejected(built):
     assert b"NULL handle" in lib.cg_last_error(None)
     assert lib.cg_selftest_wait_timeout(0, ctypes.byref(i32)) == cg.CG_EINVAL
     d = ctypes.c_double(0.0)
-    assert lib.cg_dot_host(None, 0, None, None, ctypes.byref(d)) == cg.CG_EINVAL
+    assert lib.cg_dot_host(-1, None, None, ctypes.byref(d), None) == cg.CG_EINVAL
+    assert lib.cg_dot_host(5, None, None, ctypes.byref(d), None) == cg.CG_EINVAL
+    assert lib.cg_dot(3, None, None, None, None) == cg.CG_EINVAL
+    assert lib.cg_axpy(-2, 1.0, None, None, None) == cg.CG_EINVAL
+    assert lib.cg_ewmul(4, None, None, None, None) == cg.CG_EINVAL
+    assert lib.cg_probe_fp64_peak(0, None) == cg.CG_EINVAL
+    assert lib.cg_blas_release() == cg.CG_OK

@@ -3,9 +3,9 @@
 Some callers cannot call cudaMalloc when they need a result: code that runs
 under a fixed memory budget with no allocation after start-up, code called
 from inside another allocator, or latency-critical loops that cannot take
-cudaMalloc's device synchronisation.  cg_dot needs a handle, and creating one
-allocates; cg_dot_noalloc takes raw device pointers and keeps its scratch in a
-fixed array inside the library.  These tests call it through the C ABI and
+cudaMalloc's device synchronisation.  cg_dot allocates its scratch on its first
+call for each stream; cg_dot_noalloc takes raw device pointers and keeps its
+scratch in a fixed array inside the library.  These tests call it through the C ABI and
 compare it with cg_dot on two calls in a row.  The file is named to be
 collected last, so a run stopping at the first failure has run everything
 else first; it also passes alone in a fresh process.
@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import fe_inputs as fi
-from gpu_util import cg_mod, handle
+from gpu_util import cg_mod
 
 pytestmark = pytest.mark.gpu
 
@@ -33,10 +33,9 @@ def test_noalloc_matches_cg_dot_twice(n):
     x, y = fi.uniform(n, 11, n), fi.uniform(n, 12, n)
     xd, yd = _cuda(x), _cuda(y)
     scale = float(np.sum(np.abs(x * y)))
-    with handle(fi.laplace7(3)) as h:
-        ref = torch.zeros(1, dtype=torch.float64, device="cuda")
-        cg.cg_dot(h, xd, yd, ref)
-        torch.cuda.synchronize()
+    ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cg.cg_dot(xd, yd, ref)
+    torch.cuda.synchronize()
     got = []
     for _ in range(2):  # two calls in a row share (and must clean) the scratch
         out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
