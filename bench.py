@@ -845,9 +845,16 @@ def run_variants(args, cg, A, xs, x64, dev, stream, energy, hbm, fp64, fp64_line
         s["h"].close()
     systems.clear()
     torch.cuda.empty_cache()
-    guarded("serve_100rps_mixed", lambda: serve_record(cg, args.seed, 100.0, 1.0, dev, stream, energy, hbm[0],
-                                                      "mixed", "none", budget_gb=args.budget_gb, chunk=args.chunk,
-                                                      autotune=True, group_target_ms=args.group_target_ms))
+    # the configured stream (2000 requests/s, beyond one GPU's capacity: the
+    # sustained rate and the latency under overload) over a quarter second,
+    # and a lighter one (100 requests/s) with groups sized for 10 ms solo
+    # solves, for latency below capacity
+    guarded("serve_2000rps_mixed", lambda: serve_record(cg, args.seed, 2000.0, 0.25, dev, stream, energy, hbm[0],
+                                                       "mixed", "none", budget_gb=args.budget_gb, chunk=args.chunk,
+                                                       autotune=True, group_target_ms=args.group_target_ms))
+    guarded("serve_100rps_mixed_10ms", lambda: serve_record(cg, args.seed + 1, 100.0, 1.0, dev, stream, energy,
+                                                           hbm[0], "mixed", "none", budget_gb=args.budget_gb,
+                                                           chunk=args.chunk, autotune=True, group_target_ms=10))
     return out
 
 
@@ -920,7 +927,7 @@ def batch_record(cg, systems, dev, stream, energy, hbm_peak, precision, precond,
                   preconditioner=cg.CG_PRECOND_JACOBI if jac else cg.CG_PRECOND_NONE, autotune=autotune,
                   group_target_ms=group_target_ms)
     model = {k: bt.stats()[k] for k in ("autotuned", "cta_bytes_per_s", "group_cta_bytes_per_s", "step_overhead_s",
-                                        "group_step_overhead_s")}
+                                        "group_step_overhead_s", "shape_tuned", "step_kind")}
 
     def step():
         reqs = [cg.Request(s["rp"], s["ci"], s["va"], s["b"], s["x"], tol=TOL, maxit=10 * s["n"], tag=i)

@@ -311,12 +311,19 @@ typedef struct {
   int32_t validate;        /* 1 (default): check each request's CSR on the host */
   int32_t preconditioner;  /* cg_preconditioner of every system (a non-positive diagonal
                               ends that request with CG_EINVAL) */
-  int32_t autotune;        /* 1: measure the group-size cost model on this GPU at creation
-                              (a few rounds of synthetic systems, well under a second);
-                              0 (default): built-in constants */
+  int32_t autotune;        /* 1: at creation, measure on this GPU which step shape (one lane,
+                              two lanes or a warp per row) the product runs fastest with for
+                              each bucket of row lengths, then the group-size cost model, with
+                              synthetic systems (about a second of rounds); 0 (default):
+                              built-in shapes and constants */
   int32_t group_target_ms; /* solo solve time the automatic group size aims at (default 50:
                               smaller favours latency, larger favours throughput) */
-  int32_t reserved[3];     /* zero */
+  int32_t step_shape;      /* 0 (default): the built-in step shapes, or the measured ones with
+                              autotune; 1: the built-in shapes (one lane per row up to 32
+                              entries, two lanes up to 64) even with autotune; 2: two lanes per
+                              row up to 64 entries; 3: a warp per row.  Rows of more than 64
+                              entries always take a warp each. */
+  int32_t reserved[2];     /* zero */
 } cg_batch_opts;
 
 /* One system to solve: A x = b from x0 = 0. */
@@ -362,7 +369,13 @@ typedef struct {
   double step_overhead_s;          /* per step, G = 1 */
   double group_step_overhead_s;    /* per step, G > 1 */
   int32_t autotuned;               /* 1 if the model was measured */
-  int32_t pad;
+  /* step shapes of the product (measured with autotune, else built in): the
+   * kind of step rows of (0,8], (8,16], (16,24], (24,32], (32,48], (48,64]
+   * entries go to: 0 = one lane per row (up to 32 rows per warp step), 1 = two
+   * lanes per row (up to 16 rows), 2 = one warp per row.  Rows of more than
+   * 64 entries always take a warp each. */
+  int32_t shape_tuned;             /* 1 if the step shapes were measured */
+  int32_t step_kind[6];
 } cg_batch_stats;
 
 /* Fill *o with the defaults above. */

@@ -47,7 +47,8 @@ class cg_batch_opts(ctypes.Structure):
                 ("max_pending", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("group_override", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("preconditioner", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("group_target_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("group_target_ms", ctypes.c_int32), ("step_shape", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class cg_request(ctypes.Structure):
@@ -70,7 +71,8 @@ class cg_batch_stats(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("round_ms_total", ctypes.c_double),
                 ("last_round_ms", ctypes.c_double), ("cta_bytes_per_s", ctypes.c_double),
                 ("group_cta_bytes_per_s", ctypes.c_double), ("step_overhead_s", ctypes.c_double),
-                ("group_step_overhead_s", ctypes.c_double), ("autotuned", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("group_step_overhead_s", ctypes.c_double), ("autotuned", ctypes.c_int32),
+                ("shape_tuned", ctypes.c_int32), ("step_kind", ctypes.c_int32 * 6)]
 
 
 def _load() -> ctypes.CDLL:
@@ -452,7 +454,7 @@ class Batch:
                  chunk_iters: int = 0, replace_every: int = 50, wait_limit_ms: int = 2000,
                  max_pending: int = 65536, use_graph: bool = True, group_override: int = 0,
                  validate: bool = True, device: int = -1, preconditioner: int = CG_PRECOND_NONE,
-                 autotune: bool = False, group_target_ms: int = 50):
+                 autotune: bool = False, group_target_ms: int = 50, step_shape: int = 0):
         o = cg_batch_opts()
         lib.cg_batch_opts_default(ctypes.byref(o))
         o.device, o.precision, o.budget_bytes = int(device), int(precision), int(budget_bytes)
@@ -462,6 +464,7 @@ class Batch:
         o.preconditioner = int(preconditioner)
         o.autotune = 1 if autotune else 0
         o.group_target_ms = int(group_target_ms)
+        o.step_shape = int(step_shape)
         out = ctypes.c_void_p(0)
         st = lib.cg_batch_create(ctypes.byref(out), ctypes.byref(o))
         if st != CG_OK:
@@ -515,7 +518,9 @@ class Batch:
     def stats(self) -> dict:
         s = cg_batch_stats()
         self._check(lib.cg_batch_get_stats(self._b, ctypes.byref(s)))
-        return {f: getattr(s, f) for f, _ in cg_batch_stats._fields_}
+        out = {f: getattr(s, f) for f, _ in cg_batch_stats._fields_}
+        out["step_kind"] = list(s.step_kind)
+        return out
 
     def group_for(self, row_ptr) -> int:
         import numpy as np

@@ -212,6 +212,9 @@ struct cg_batch_ctx {
   int group_override = 0;
   int calib_group = 0;        // group of the calibration requests (while calibrating)
   bool autotuned = false;
+  cgh::StepShape shape;       // step kind per row length of every admitted system
+  bool shape_tuned = false;
+  bool shape_fixed = false;   // set by cg_batch_opts.step_shape (not tuned)
   bool validate = true;
   int nblocks = 0;
   int task_cap = 0;
@@ -435,8 +438,13 @@ void admit(cg_batch_ctx* b) {
     const int group = b->calib_group > 0      ? std::min(b->calib_group, b->nblocks)
                       : b->group_override > 0 ? std::min(b->group_override, b->nblocks)
                                               : auto_group(b->model, n, nnz, b->mixed, b->nblocks);
+    cgh::StepShape shape;
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      shape = b->shape;
+    }
     cgh::Partition part;
-    cgh::build_partition(rp, n, group, part);
+    cgh::build_partition(rp, n, group, part, shape);
     const Layout L = layout_of(n, nnz, part.step.size(), group, b->mixed, b->jacobi);
     size_t off = 0;
     int slot = -1;
@@ -830,13 +838,80 @@ double time_per_step(cg_batch_ctx* b, const std::vector<int32_t>& rp, const std:
   return (s1.round_ms_total - s0.round_ms_total) * 1e-3 / steps;
 }
 
+// Banded system of n rows with rows of L entries inside (L odd): columns
+// i - (L-1)/2 .. i + (L-1)/2, diagonal L + 1, the others -1 (strictly
+// diagonally dominant, hence SPD).  A timing workload of the calibration only.
+void banded(int64_t n, int L, std::vector<int32_t>& rp, std::vector<int32_t>& ci, std::vector<double>& va) {
+  const int64_t h = (L - 1) / 2;
+  rp.assign(static_cast<size_t>(n) + 1, 0);
+  ci.clear();
+  va.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = std::max<int64_t>(0, i - h); j <= std::min<int64_t>(n - 1, i + h); ++j) {
+      ci.push_back(static_cast<int32_t>(j));
+      va.push_back(j == i ? static_cast<double>(L + 1) : -1.0);
+    }
+    rp[static_cast<size_t>(i) + 1] = static_cast<int32_t>(ci.size());
+  }
+}
+
+// Row-length buckets of the step-shape table: rows of (kShapeLo[k], kShapeHi[k]]
+// entries share one step kind, measured on a banded system whose rows have
+// kShapeRep[k] entries.
+constexpr int kShapeBuckets = 6;
+constexpr int kShapeHi[kShapeBuckets] = {8, 16, 24, 32, 48, 64};
+constexpr int kShapeRep[kShapeBuckets] = {7, 15, 23, 31, 47, 63};
+
+// The autotuner of the step shapes: for each bucket of row lengths, time one
+// copy per CTA of a banded system with such rows (one CTA each, every SM busy,
+// a fixed number of steps) with each step kind the rows allow (one lane or
+// two lanes per row up to 32 entries, two lanes or a warp per row above), and
+// keep the kind of the shortest time; the built-in kind stays unless another
+// is at least 2 % faster.  The table then applies to every system the batch
+// object admits, so a system's partition still depends on the system alone.
+void calibrate_shape(cg_batch_ctx* b) {
+  constexpr int kSteps = 40;
+  cgh::StepShape best;  // the built-in table
+  bool measured_all = true;
+  for (int k = 0; k < kShapeBuckets; ++k) {
+    const int L = kShapeRep[k];
+    std::vector<int32_t> rp, ci;
+    std::vector<double> va;
+    banded(static_cast<int64_t>(131072) / L, L, rp, ci, va);
+    const int lo = k == 0 ? 0 : kShapeHi[k - 1] + 1;
+    const int cand[2] = {L <= cgk::kLaneMax ? cgk::kLanePerRow : cgk::kPairPerRow,
+                         L <= cgk::kLaneMax ? cgk::kPairPerRow : cgk::kLongRow};
+    double t[2] = {-1.0, -1.0};
+    for (int c = 0; c < 2; ++c) {
+      cgh::StepShape trial = best;
+      for (int len = lo; len <= kShapeHi[k]; ++len) trial.mode[len] = static_cast<int8_t>(cand[c]);
+      {
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->shape = trial;
+      }
+      t[c] = time_per_step(b, rp, ci, va, b->nblocks, 1, kSteps);
+    }
+    if (t[0] <= 0 || t[1] <= 0) {
+      measured_all = false;
+      continue;
+    }
+    const int pick = t[1] < 0.98 * t[0] ? cand[1] : cand[0];
+    for (int len = lo; len <= kShapeHi[k]; ++len) best.mode[len] = static_cast<int8_t>(pick);
+  }
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->shape = best.valid() ? best : cgh::StepShape();
+  b->shape_tuned = measured_all && best.valid();
+}
+
 // The autotuner of the group size: measure the cost model's rates and
 // per-step overheads on this GPU with synthetic 27-point systems, all CTAs
 // busy.  One-CTA systems of two sizes give the rate and overhead of G = 1
 // (time per step = bytes / rate + overhead); one size solved by groups of 8
 // and of 16 CTAs gives those of groups.  Any measurement that fails or is
-// inconsistent keeps the built-in value.
+// inconsistent keeps the built-in value.  The step shapes are tuned first,
+// and the group model is measured with them.
 void calibrate(cg_batch_ctx* b) {
+  if (!b->shape_fixed) calibrate_shape(b);
   std::vector<int32_t> rp0, ci0, rp1, ci1, rp2, ci2;
   std::vector<double> va0, va1, va2;
   stencil27(10, rp0, ci0, va0);
@@ -916,9 +991,17 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
   if (o.max_systems <= 0 || o.max_systems > (1 << 20) || o.chunk_iters < 0 || o.replace_every < 0 ||
       o.budget_bytes < 0 || o.max_pending <= 0 || o.group_override < 0 ||
       (o.preconditioner != CG_PRECOND_NONE && o.preconditioner != CG_PRECOND_JACOBI) || o.autotune < 0 ||
-      o.autotune > 1 || o.group_target_ms <= 0)
+      o.autotune > 1 || o.group_target_ms <= 0 || o.step_shape < 0 || o.step_shape > 3)
     return bfail(nullptr, CG_EINVAL, "cg_batch_create: bad option");
   auto b = std::make_unique<cg_batch_ctx>();
+  if (o.step_shape > 0) {
+    // 1: the built-in shapes; 2: two lanes per row up to 64 entries; 3: a warp per row
+    for (int L = 0; L <= cgh::kShapeMaxLen; ++L) {
+      if (o.step_shape == 2) b->shape.mode[L] = static_cast<int8_t>(cgk::kPairPerRow);
+      if (o.step_shape == 3) b->shape.mode[L] = static_cast<int8_t>(cgk::kLongRow);
+    }
+    b->shape_fixed = true;
+  }
   if (o.device >= 0) b->device = o.device;
   else if (cudaGetDevice(&b->device) != cudaSuccess) return bfail(nullptr, CG_ECUDA, "cg_batch_create: no device");
   if (cudaSetDevice(b->device) != cudaSuccess) {
@@ -1109,7 +1192,8 @@ int cg_batch_get_stats(cg_batch b, cg_batch_stats* st) {
   st->step_overhead_s = b->model.overhead_1;
   st->group_step_overhead_s = b->model.overhead_g;
   st->autotuned = b->autotuned ? 1 : 0;
-  st->pad = 0;
+  st->shape_tuned = b->shape_tuned ? 1 : 0;
+  for (int k = 0; k < kShapeBuckets; ++k) st->step_kind[k] = b->shape.mode[kShapeHi[k]];
   return CG_OK;
 }
 

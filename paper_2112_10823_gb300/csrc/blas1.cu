@@ -206,8 +206,12 @@ int dot_stream_grid(int64_t n, int num_sms) {
 // thread runs eight independent FMA chains a = a * m + c, whose fixed point is
 // c / (1 - m) = 1, so the values stay finite; the sum is stored only if it
 // takes a value it cannot take, which keeps the compiler from dropping the
-// work without writing anything.
-__global__ void __launch_bounds__(256) fp64_probe_kernel(int64_t iters, double m, double c, double* sink) {
+// work without writing anything.  m and c are moved into registers first
+// (adding 1e-300 * threadIdx.x changes neither value but hides that from
+// the compiler): with an operand read from the constant bank, FMAs issue at
+// only 1.68 per clock per SM on GB300 instead of 2.
+__global__ void __launch_bounds__(256) fp64_probe_kernel(int64_t iters, double m_in, double c_in, double* sink) {
+  const double m = m_in + 1e-300 * threadIdx.x, c = c_in + 1e-300 * blockIdx.x;
   double a[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) a[k] = 0.5 + 1e-3 * k + 1e-9 * threadIdx.x;

@@ -49,11 +49,25 @@ int64_t cost_split(const std::vector<int32_t>& rp, int64_t lo_row, int64_t hi_ro
   return lo;
 }
 
-void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partition& P) {
-  const int64_t kPairMax = 2 * cgk::kLaneMax;
+StepShape::StepShape() {
+  for (int L = 0; L <= kShapeMaxLen; ++L)
+    mode[L] = static_cast<int8_t>(L <= cgk::kLaneMax ? cgk::kLanePerRow : cgk::kPairPerRow);
+}
+
+bool StepShape::valid() const {
+  for (int L = 0; L <= kShapeMaxLen; ++L) {
+    const int m = mode[L];
+    if (m != cgk::kLanePerRow && m != cgk::kPairPerRow && m != cgk::kLongRow) return false;
+    if (m == cgk::kLanePerRow && L > cgk::kLaneMax) return false;
+  }
+  return true;
+}
+
+void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, const StepShape& shape, Partition& P) {
+  auto kind = [&](int64_t len) -> int { return len > kShapeMaxLen ? cgk::kLongRow : shape.mode[len]; };
   while (row < end) {
     const int64_t len0 = rp[row + 1] - rp[row];
-    if (len0 > kPairMax) {  // a long row: one step, walked piece by piece
+    if (kind(len0) == cgk::kLongRow) {  // a warp per row: one step, walked piece by piece
       P.step.push_back(make_int4(static_cast<int>(row), static_cast<int>(row + 1), rp[row], rp[row + 1]));
       P.step_mode.push_back(cgk::kLongRow);
       ++row;
@@ -61,25 +75,26 @@ void warp_steps(const std::vector<int32_t>& rp, int64_t row, int64_t end, Partit
     }
     const int64_t start = row;
     int64_t cnt = 0, maxlen = 0;
+    int m = cgk::kLanePerRow;  // the widest kind so far (one lane < two lanes)
     while (row < end) {
       const int64_t len = rp[row + 1] - rp[row];
-      if (len > kPairMax || cnt + len > cgk::kStepNnz) break;
-      const int64_t nm = std::max(maxlen, len);
-      const int64_t cap = nm <= cgk::kLaneMax ? 32 : 16;
+      const int k = kind(len);
+      if (k == cgk::kLongRow || cnt + len > cgk::kStepNnz) break;
+      const int nm = std::max(m, k);
+      const int64_t cap = nm == cgk::kLanePerRow ? 32 : 16;
       if (row - start + 1 > cap) break;
       cnt += len;
-      maxlen = nm;
+      maxlen = std::max(maxlen, len);
+      m = nm;
       ++row;
     }
     P.step.push_back(make_int4(static_cast<int>(start), static_cast<int>(row), rp[start], rp[row]));
-    const bool lane_mode = maxlen <= cgk::kLaneMax;
-    const int64_t wmax = lane_mode ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
-    P.step_mode.push_back((lane_mode ? cgk::kLanePerRow : cgk::kPairPerRow) |
-                          static_cast<int32_t>(wmax << cgk::kWmaxShift));
+    const int64_t wmax = m == cgk::kLanePerRow ? maxlen : (maxlen + 1) / 2;  // longest segment of one lane
+    P.step_mode.push_back(m | static_cast<int32_t>(wmax << cgk::kWmaxShift));
   }
 }
 
-void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P) {
+void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P, const StepShape& shape) {
   P.step.clear();
   P.step_mode.clear();
   P.block_step.assign(static_cast<size_t>(nblocks) + 1, 0);
@@ -88,7 +103,7 @@ void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Par
   P.block_row[nblocks] = static_cast<int32_t>(n);
   for (int b = 0; b < nblocks; ++b) {
     P.block_step[b] = static_cast<int32_t>(P.step.size());
-    warp_steps(rp, P.block_row[b], P.block_row[b + 1], P);
+    warp_steps(rp, P.block_row[b], P.block_row[b + 1], shape, P);
   }
   P.block_step[nblocks] = static_cast<int32_t>(P.step.size());
   for (int t = 0; t < 2; ++t) {  // sentinels

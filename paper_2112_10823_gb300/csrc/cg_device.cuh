@@ -44,6 +44,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// The same copy with an L2 eviction policy (createpolicy): used for data read
+// once per pass, so that it does not push reused data out of L2.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -437,6 +454,7 @@ __device__ __forceinline__ bool producer_loop(const RingSmem& sm, const CtaStrea
                                               const int32_t* col, int max_passes, unsigned long long limit_ns) {
   bool ok = true;
   uint32_t g = 0;
+  const uint64_t pol = l2_evict_first_policy();
   if (cs.npieces > 0) {
     const int ke4 = (cs.ke + 3) & ~3;  // copy whole 16-byte groups (<= 3 padding entries)
     for (int pass = 0; ok && (max_passes < 0 || pass < max_passes); ++pass) {
@@ -455,11 +473,11 @@ __device__ __forceinline__ bool producer_loop(const RingSmem& sm, const CtaStrea
         const int nm = slot == 0 ? (e1 - e0 < kMirror ? e1 - e0 : kMirror) : 0;  // a multiple of 4
         const uint32_t mv = static_cast<uint32_t>(nm) * sizeof(T), mc = static_cast<uint32_t>(nm) * 4u;
         mbar_arrive_expect_tx(sm.full(slot), bv + bc + mv + mc);
-        bulk_g2s(sm.val<T>() + pos, val + e0, bv, sm.full(slot));
-        bulk_g2s(sm.col() + pos, col + e0, bc, sm.full(slot));
+        bulk_g2s_hint(sm.val<T>() + pos, val + e0, bv, sm.full(slot), pol);
+        bulk_g2s_hint(sm.col() + pos, col + e0, bc, sm.full(slot), pol);
         if (nm) {
-          bulk_g2s(sm.val<T>() + kRing, val + e0, mv, sm.full(slot));
-          bulk_g2s(sm.col() + kRing, col + e0, mc, sm.full(slot));
+          bulk_g2s_hint(sm.val<T>() + kRing, val + e0, mv, sm.full(slot), pol);
+          bulk_g2s_hint(sm.col() + kRing, col + e0, mc, sm.full(slot), pol);
         }
       }
     }

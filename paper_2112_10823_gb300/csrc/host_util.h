@@ -17,6 +17,20 @@ struct Partition {
   std::vector<int32_t> block_row;
 };
 
-void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P);
+// Which kind of step (cgk::StepMode: one lane per row, two lanes per row, or
+// a warp per row) rows of each length 0..64 go to; longer rows always take a
+// warp each.  A step's kind is the widest kind among its rows; a one-lane
+// step holds up to 32 rows, a two-lane step up to 16.  The built-in table is
+// one lane for rows of up to 32 entries and two lanes for 33..64.  A lane
+// computes at most 32 entries, so mode[L] may be "one lane" only for L <= 32.
+constexpr int kShapeMaxLen = 64;
+struct StepShape {
+  int8_t mode[kShapeMaxLen + 1];
+  StepShape();
+  bool valid() const;
+};
+
+void build_partition(const std::vector<int32_t>& rp, int64_t n, int nblocks, Partition& P,
+                     const StepShape& shape = StepShape());
 
 }  // namespace cgh

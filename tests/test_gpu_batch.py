@@ -325,6 +325,51 @@ def test_autotuned_group_model():
         _check_vs_oracle(A, b, r, _x(req))
 
 
+def test_autotuned_step_shapes():
+    """The autotuner also measures, for each bucket of row lengths, which step
+    shape (one lane, two lanes or a warp per row) the product runs fastest
+    with on this GPU.  The table holds only shapes the rows allow; systems
+    solved with it match the oracle; a system gives the same bits alone and
+    in a mix on the tuned object (the table depends on the object, not the mix)."""
+    cg = cg_mod()
+    with cg.Batch(autotune=True) as bt:
+        st = bt.stats()
+        assert st["shape_tuned"] == 1
+        kinds = st["step_kind"]
+        assert all(k in (0, 1) for k in kinds[:4]) and all(k in (1, 2) for k in kinds[4:]), kinds
+        systems = [_system(N, 1500 + N) for N in (5, 9, 13)] + [_system(7, 1507, "lap7")]
+        reqs = [_request(A, b) for A, b in systems]
+        res = _wait_all(bt, bt.submit(reqs))
+        A1, b1 = systems[1]
+        alone = _request(A1, b1)
+        _wait1(bt, bt.submit([alone])[0])
+    for (A, b), req, r in zip(systems, reqs, res):
+        _check_vs_oracle(A, b, r, _x(req))
+    assert np.array_equal(_x(alone), _x(reqs[1]))
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_forced_step_shapes(shape):
+    """Every step shape (1: the built-in one lane per row up to 32 entries and
+    two lanes up to 64; 2: two lanes per row; 3: a warp per row) solves Q1
+    systems, a 7-point Laplacian and an irregular SPD system with rows of 14
+    to 37 entries to the oracle's result at equal steps; the stats report the shape."""
+    cg = cg_mod()
+    irregular = fi.random_spd(300, 77, density=0.08)
+    xs = fi.xstar(77, irregular.n)
+    systems = [_system(6, 1601), _system(11, 1602), _system(9, 1603, "lap7"),
+               (irregular, oracle.spmv(irregular, xs))]
+    with cg.Batch(step_shape=shape, autotune=True) as bt:
+        st = bt.stats()
+        assert st["shape_tuned"] == 0
+        want = {1: [0, 0, 0, 0, 1, 1], 2: [1] * 6, 3: [2] * 6}[shape]
+        assert st["step_kind"] == want
+        reqs = [_request(A, b) for A, b in systems]
+        res = _wait_all(bt, bt.submit(reqs))
+    for (A, b), req, r in zip(systems, reqs, res):
+        _check_vs_oracle(A, b, r, _x(req))
+
+
 def test_destroy_with_work_in_flight():
     """Destroying a batch object while requests are queued and running
     returns after the round in flight; a new batch object then works."""
