@@ -12,7 +12,7 @@ Functions follow the paper's definitions:
   cg     classical unpreconditioned CG (Sec. 5.3), Hestenes-Stiefel form
   cg_mixed   FP32-matrix product with FP64 scalars and residual replacement
   matrix_stats  the columns of the paper's Table 1 (Sec. 5.1)
-  omp_cg / omp_spmv / omp_dot   the same CG and product spread over the host's
+  omp_cg / omp_cg_mixed / omp_spmv / omp_dot   the same CG (FP64 and mixed) and product spread over the host's
              cores with OpenMP (``cg_oracle_omp.c``): the timing variant behind
              the CPU baseline, pinned against the sequential functions
 """
@@ -126,6 +126,8 @@ def _load_omp():
             lib.oracle_omp_dot.argtypes = [i64, vp, vp]
             lib.oracle_omp_cg.restype = ci
             lib.oracle_omp_cg.argtypes = [i64, vp, vp, vp, ci, vp, vp, dbl, i64, i64, vp, vp, vp]
+            lib.oracle_omp_cg_mixed.restype = ci
+            lib.oracle_omp_cg_mixed.argtypes = [i64, vp, vp, vp, vp, ci, vp, vp, dbl, i64, i64, i64, vp, vp, vp]
             _omp_lib = lib
     return _omp_lib
 
@@ -360,4 +362,21 @@ def omp_cg(A, b, tol: float = 1e-10, maxit: int | None = None, x0=None, force_it
     st = _need_omp().oracle_omp_cg(n, _p(rp), _p(ci), _p(va), int(getattr(A, "index_base", 0)), _p(b), _p(x),
                                    float(tol), int(maxit), int(force_iters), ctypes.byref(it), ctypes.byref(rr),
                                    ctypes.byref(rt))
+    return CGResult(x, st, it.value, rr.value, rt.value)
+
+
+def omp_cg_mixed(A, b, tol: float = 1e-10, maxit: int | None = None, replace_every: int = 50,
+                 force_iters: int = -1) -> CGResult:
+    """Mixed-precision CG on all host cores (the steps of ``cg_mixed``);
+    ``force_iters >= 0`` runs exactly that many steps."""
+    n = A.n
+    rp, ci, va, b = _i32(A.row_ptr), _i32(A.col_idx), _f64(A.val), _f64(b)
+    v32 = va.astype(np.float32)
+    x = np.zeros(n)
+    maxit = 10 * n if maxit is None else maxit
+    it = ctypes.c_int64(0)
+    rr, rt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = _need_omp().oracle_omp_cg_mixed(n, _p(rp), _p(ci), _p(va), _p(v32), int(getattr(A, "index_base", 0)),
+                                         _p(b), _p(x), float(tol), int(maxit), int(replace_every), int(force_iters),
+                                         ctypes.byref(it), ctypes.byref(rr), ctypes.byref(rt))
     return CGResult(x, st, it.value, rr.value, rt.value)

@@ -143,3 +143,85 @@ int oracle_omp_cg(int64_t n, const int32_t* IA, const int32_t* JA, const double*
     free(r); free(p); free(q); free(part);
     return status;
 }
+
+/*
+ * Mixed-precision CG with residual replacement, the steps and outputs of
+ * oracle_cg_mixed in cg_oracle.c (FP32 values AA32 and FP32-accumulated
+ * product, each row in storage order; FP64 dots, scalars, x, r and p; r
+ * replaced by the FP64 true residual every replace_every steps and whenever
+ * the recursive residual reaches tol*||b||, the direction keeping the
+ * recurrence's beta; convergence on the true residual; force_iters >= 0 runs
+ * exactly that many steps) with every vector loop spread over the host's
+ * cores.  The FP32 and FP64 products are the sequential oracle's to the bit;
+ * the dots are summed in T blocks added in block order.
+ */
+int oracle_omp_cg_mixed(int64_t n, const int32_t* IA, const int32_t* JA, const double* AA, const float* AA32,
+                        int base, const double* b, double* x, double tol, int64_t maxit, int64_t replace_every,
+                        int64_t force_iters, int64_t* iters, double* relres_rec, double* relres_true) {
+    size_t m = (size_t)(n > 0 ? n : 1);
+    int T = omp_get_max_threads();
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* p = (double*)malloc(sizeof(double) * m);
+    double* q = (double*)malloc(sizeof(double) * m);
+    float* p32 = (float*)malloc(sizeof(float) * m);
+    double* part = (double*)malloc(sizeof(double) * (size_t)T);
+    if (!r || !p || !q || !p32 || !part) { free(r); free(p); free(q); free(p32); free(part); return ORC_NOMEM; }
+    int status = ORC_OK;
+    double bnorm = sqrt(omp_dot(n, b, b, part, T));
+    *iters = 0;
+    if (bnorm == 0.0) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        *relres_rec = 0.0; *relres_true = 0.0;
+        free(r); free(p); free(q); free(p32); free(part);
+        return ORC_OK;
+    }
+    oracle_omp_spmv(n, IA, JA, AA, base, x, q);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
+    double rho = omp_dot(n, r, r, part, T);
+    int64_t k = 0;
+    int done = (force_iters < 0) && (sqrt(rho) <= tol * bnorm);
+    int64_t limit = force_iters >= 0 ? force_iters : maxit;
+    while (!done && k < limit) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) p32[i] = (float)p[i];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            float s = 0.0f;
+            for (int64_t kk = (int64_t)IA[i] - base; kk < (int64_t)IA[i + 1] - base; ++kk)
+                s = s + AA32[kk] * p32[JA[kk] - base];
+            q[i] = (double)s;
+        }
+        double gamma = omp_dot(n, p, q, part, T);
+        if (!(gamma > 0.0) || !isfinite(gamma)) { status = ORC_BREAKDOWN; break; }
+        double alpha = rho / gamma;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+        double rho_new = omp_dot(n, r, r, part, T);
+        double beta = rho_new / rho;
+        k = k + 1;
+        int replace = (replace_every > 0 && k % replace_every == 0) || sqrt(rho_new) <= tol * bnorm;
+        if (replace) {
+            oracle_omp_spmv(n, IA, JA, AA, base, x, q);
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+            rho_new = omp_dot(n, r, r, part, T);
+            if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rho = rho_new;
+    }
+    *iters = k;
+    *relres_rec = sqrt(rho) / bnorm;
+    if (status == ORC_OK && force_iters < 0 && !done) status = ORC_NOTCONV;
+    oracle_omp_spmv(n, IA, JA, AA, base, x, q);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+    *relres_true = sqrt(omp_dot(n, q, q, part, T)) / bnorm;
+    free(r); free(p); free(q); free(p32); free(part);
+    return status;
+}

@@ -408,11 +408,12 @@ def pin_pcg_jacobi():
 
 def pin_omp_variant():
     """The OpenMP timing variant against the sequential oracle (itself pinned
-    above) and against mathematics: with one thread the same bits for CG and
-    the product; with every host core the product's bits, iterates at equal
-    step counts within 1e-9 relative (the dot products' block order is the
-    only difference), stopping steps within max(2, 1 %); the 7-point
-    Laplacian's Chebyshev step bound; b = 0 and breakdown."""
+    above) and against mathematics: with one thread the same bits for CG,
+    mixed-precision CG and the product; with every host core the product's
+    bits, iterates at equal step counts within 1e-9 relative (the dot
+    products' block order is the only difference), stopping steps within
+    max(2, 1 %) (mixed: max(5, 5 %)); the mixed run's replacement schedule;
+    the 7-point Laplacian's Chebyshev step bound; b = 0 and breakdown."""
     if not oracle.omp_available():
         import pytest
         pytest.skip("no OpenMP on this host compiler")
@@ -437,6 +438,28 @@ def pin_omp_variant():
                     assert np.linalg.norm(par.x - same.x) <= 1e-9 * np.linalg.norm(same.x)
                     exact = math.fsum((b * b).tolist())
                     assert abs(oracle.omp_dot(b, b) - exact) <= 2 * A.n * 2.0 ** -53 * exact
+        # the mixed-precision iteration: bitwise the sequential one with one
+        # thread; on every core the same iterates at equal steps within 1e-9 and
+        # stopping steps within max(5, 5 %) (the mixed stop's own spread)
+        Am = fi.q1(12, 1.0, 5)
+        bm = oracle.spmv(Am, fi.xstar(5, Am.n))
+        for T in (1, max(full, 3)):
+            oracle.omp_set_threads(T)
+            seqm = oracle.cg_mixed(Am, bm, tol=1e-10, replace_every=20)
+            parm = oracle.omp_cg_mixed(Am, bm, tol=1e-10, replace_every=20)
+            assert parm.status == oracle.OK and parm.relres_true <= 1e-10 * 1.0000001
+            if T == 1:
+                assert parm.iters == seqm.iters and np.array_equal(parm.x, seqm.x)
+                assert parm.relres_rec == seqm.relres_rec
+            else:
+                assert abs(parm.iters - seqm.iters) <= max(5, math.ceil(0.05 * seqm.iters))
+                same = oracle.cg_mixed(Am, bm, tol=1e-10, replace_every=20, force_iters=parm.iters)
+                assert np.linalg.norm(parm.x - same.x) <= 1e-9 * np.linalg.norm(same.x)
+            forced = oracle.omp_cg_mixed(Am, bm, tol=1e-30, replace_every=4, force_iters=8)
+            assert forced.iters == 8 and forced.relres_rec == forced.relres_true
+            beyond = oracle.omp_cg_mixed(Am, bm, tol=1e-10, replace_every=20, force_iters=parm.iters + 5)
+            assert beyond.iters == parm.iters + 5 and beyond.relres_true <= 1e-9
+        oracle.omp_set_threads(full)
         N = 16
         A = fi.laplace7(N)
         lmin = 12.0 * math.sin(math.pi / (2 * (N + 1))) ** 2

@@ -259,3 +259,30 @@ def test_mixed_equal_iterations_vs_mixed_oracle(N, seed):
     ref = oracle.cg_mixed(A, b, tol=1e-10, replace_every=50)
     assert ref.status == oracle.OK
     assert abs(res.iters - ref.iters) <= max(5, 0.05 * ref.iters), (res.iters, ref.iters)
+
+
+def test_q1_n160_mixed_equal_iterations():
+    """The mixed arm of the 160^3 configuration: the GPU's mixed solve against
+    the mixed oracle on all host cores (pinned against the sequential mixed
+    oracle) for exactly the GPU's step count, 1e-8 in norm and element by
+    element against the largest entry; stopping steps within max(5, 5 %); the
+    FP64 true residual recomputed by the oracle <= 1e-10."""
+    import torch
+    cg = cg_mod()
+    if not oracle.omp_available():
+        pytest.skip("the OpenMP oracle is not built on this host")
+    A = fi.q1(160, 1.0, 0)
+    b = oracle.omp_spmv(A, fi.xstar(0, A.n))
+    with handle(A, precision=cg.CG_PREC_MIXED, replace_every=50) as h:
+        res, x = solve(h, b, maxit=20000)
+    assert res.status == cg.CG_OK, res
+    true_rel = np.linalg.norm(b - oracle.omp_spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 * 1.0000001
+    same = oracle.omp_cg_mixed(A, b, tol=1e-10, replace_every=50, force_iters=res.iters)
+    assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+    assert np.max(np.abs(x - same.x)) <= 1e-8 * np.max(np.abs(same.x))
+    ref = oracle.omp_cg_mixed(A, b, tol=1e-10, maxit=20000, replace_every=50)
+    assert ref.status == oracle.OK
+    assert abs(res.iters - ref.iters) <= max(5, 0.05 * ref.iters), (res.iters, ref.iters)
+    del A
+    torch.cuda.empty_cache()

@@ -69,9 +69,16 @@ OMP_MUTANTS = [
      "for (int t = 0; t + 1 < T; ++t) s = s + part[t];"),
     ("omp_blocks_overlap", "*hi = (n * (t + 1)) / T;", "*hi = (n * (t + 1)) / T + (t + 1 < T);"),
     ("omp_spmv_drops_last_entry", "k < (int64_t)IA[i + 1] - base; ++k)", "k < (int64_t)IA[i + 1] - base - 1; ++k)"),
-    ("omp_beta_inverted", "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
-    ("omp_x_update_sign", "x[i] = x[i] + alpha * p[i];", "x[i] = x[i] - alpha * p[i];"),
-    ("omp_true_residual_sign", "q[i] = b[i] - q[i];", "q[i] = b[i] + q[i];"),
+    ("omp_beta_inverted", "{ rho = rho_new; done = 1; break; }\n        double beta = rho_new / rho;",
+     "{ rho = rho_new; done = 1; break; }\n        double beta = rho / rho_new;"),
+    ("omp_x_update_sign", "x[i] = x[i] + alpha * p[i];\n#pragma omp parallel for schedule(static)\n        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];\n        double rho_new = omp_dot(n, r, r, part, T);\n        k = k + 1;",
+     "x[i] = x[i] - alpha * p[i];\n#pragma omp parallel for schedule(static)\n        for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];\n        double rho_new = omp_dot(n, r, r, part, T);\n        k = k + 1;"),
+    ("omp_true_residual_sign", "    for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];\n    *relres_true = sqrt(omp_dot(n, q, q, part, T)) / bnorm;\n    free(r); free(p); free(q); free(part);",
+     "    for (int64_t i = 0; i < n; ++i) q[i] = b[i] + q[i];\n    *relres_true = sqrt(omp_dot(n, q, q, part, T)) / bnorm;\n    free(r); free(p); free(q); free(part);"),
+    ("omp_mixed_replacement_offset", "k % replace_every == 0", "k % replace_every == 1"),
+    ("omp_mixed_fp32_sum_in_fp64", "float s = 0.0f;", "double s = 0.0;"),
+    ("omp_mixed_forced_run_stops", "if (force_iters < 0 && sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }",
+     "if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; done = 1; break; }\n        }"),
 ]
 
 
