@@ -370,6 +370,28 @@ def common_config(args, n: int, nnz: int, world: int) -> dict:
 
 # ------------------------------------------------------- oracle (host) legs
 
+def host_cpu() -> dict:
+    """Model name and logical core count of the host (lscpu; /proc/cpuinfo as a fallback)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def oracle_solver(precision: str, precond: str = "none"):
     """The oracle that times a CPU solve: the OpenMP variant on all host cores
     for plain FP64 CG (the configurations' method), the sequential oracle for
@@ -446,7 +468,7 @@ def run_reference(args):
         "solve": {"iters": r.iters, "relres_true": r.relres_true},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} whole solves of the workload, one per step "
-                                   f"({r.iters} iterations), {who}"},
+                                   f"({r.iters} iterations), {who}", "host": host_cpu()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -741,7 +763,8 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         bh = b.cpu().numpy()
         v, cores, sample = oracle_rate(A, bh, args.precision, args.cpu_budget, iters, args.precond)
-        base = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+        base = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                "host": host_cpu()}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,

@@ -213,17 +213,25 @@ def pin_cg_laplace_bounds(N: int = 16):
 
 
 def pin_cg_orthogonality():
-    """Residuals of early steps are mutually orthogonal."""
+    """Residuals of early steps are mutually orthogonal, and the search
+    directions are A-conjugate: d_k = x_{k+1} - x_k = alpha_k p_k gives
+    d_i . A d_j = 0 for i != j (Hestenes-Stiefel)."""
     A = fi.q1(5, sigma=1.0, seed=4)
     xs = fi.xstar(4, A.n)
     b = oracle.spmv(A, xs)
-    rs = []
-    for k in range(6):
-        xk = oracle.cg(A, b, force_iters=k).x
-        rs.append(b - oracle.spmv(A, xk))
+    rs, xk = [], []
+    for k in range(7):
+        xk.append(oracle.cg(A, b, force_iters=k).x)
+        rs.append(b - oracle.spmv(A, xk[-1]))
     for i in range(6):
         for j in range(i):
             c = abs(rs[i] @ rs[j]) / (np.linalg.norm(rs[i]) * np.linalg.norm(rs[j]))
+            assert c <= 1e-8, (i, j, c)
+    d = [xk[k + 1] - xk[k] for k in range(6)]
+    Ad = [oracle.spmv(A, v) for v in d]
+    for i in range(6):
+        for j in range(i):
+            c = abs(d[i] @ Ad[j]) / math.sqrt((d[i] @ Ad[i]) * (d[j] @ Ad[j]))
             assert c <= 1e-8, (i, j, c)
 
 
