@@ -162,7 +162,8 @@ int cg_spmv(cg_handle h, const double* x, double* y);
  * device memory (cudaMalloc, so make that first call outside any stream
  * capture), which later calls on the same pair reuse and cg_blas_release()
  * frees.  Calls on one stream run in order, so they may share it; calls on
- * different streams get different scratch.  If a device-side wait of the
+ * different streams get different scratch (cudaStreamPerThread counts as a
+ * different stream in every host thread).  If a device-side wait of the
  * kernel gives up (only a fault of the copy engine could cause it), *result
  * is NaN; cg_dot_host reports it as CG_ETIMEOUT.
  */

@@ -8,6 +8,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -255,8 +257,11 @@ struct BlasScratch {
   int32_t* err;  // [0] raised by the kernel, [1] outcome of the last call
   double* result;
 };
+// Key: (device, stream, host thread).  The thread is part of the key only for
+// cudaStreamPerThread, whose one handle value names a different stream in
+// every host thread.
 std::mutex g_blas_mu;
-std::map<std::pair<int, uintptr_t>, double*> g_blas;
+std::map<std::tuple<int, uintptr_t, size_t>, double*> g_blas;
 
 int sm_count(int dev) {
   static std::mutex mu;
@@ -275,7 +280,8 @@ cudaError_t blas_scratch(cudaStream_t s, int* dev_out, BlasScratch* out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_blas_mu);
-  auto key = std::make_pair(dev, reinterpret_cast<uintptr_t>(s));
+  const size_t thread_part = s == cudaStreamPerThread ? std::hash<std::thread::id>{}(std::this_thread::get_id()) : 0;
+  auto key = std::make_tuple(dev, reinterpret_cast<uintptr_t>(s), thread_part);
   auto it = g_blas.find(key);
   double* base = nullptr;
   if (it == g_blas.end()) {
@@ -672,7 +678,7 @@ int cg_blas_release(void) {
   int cur = -1;
   cudaGetDevice(&cur);
   for (auto& kv : g_blas) {
-    cudaSetDevice(kv.first.first);
+    cudaSetDevice(std::get<0>(kv.first));
     cudaFree(kv.second);
   }
   g_blas.clear();

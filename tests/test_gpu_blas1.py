@@ -164,3 +164,35 @@ def test_fp64_peak_probe():
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     assert 0 < g
     assert g <= 2 * 2 * props.multi_processor_count * 2.2e9 / 1e9 * 1.5
+
+
+def test_dot_on_the_per_thread_default_stream_from_two_threads():
+    """cudaStreamPerThread (handle value 2) names a different stream in every
+    host thread; each thread gets its own scratch, so concurrent dot products
+    on it from two threads give their own correct sums."""
+    import threading
+    import torch
+    cg = cg_mod()
+    n = 3_000_000
+    data = [(fi.uniform(40 + t, 1, n), fi.uniform(40 + t, 2, n)) for t in range(2)]
+    dev = [(_cuda(x), _cuda(y)) for x, y in data]
+    torch.cuda.synchronize()
+    got = [[], []]
+
+    def work(t):
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(20):
+            got[t].append(cg.cg_dot_host(dev[t][0], dev[t][1], stream=2))
+        cg.cg_dot(dev[t][0], dev[t][1], out, stream=2)
+        torch.cuda.synchronize()
+        got[t].append(out.item())
+
+    th = [threading.Thread(target=work, args=(t,)) for t in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    for t, (x, y) in enumerate(data):
+        ref = oracle.dot(x, y)
+        assert len(got[t]) == 21 and len(set(got[t])) == 1, set(got[t])
+        assert abs(got[t][0] - ref) <= 1e-12 * float(np.sum(np.abs(x * y)))
