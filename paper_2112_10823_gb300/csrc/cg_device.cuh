@@ -3,6 +3,7 @@
 // barrier of the persistent solve, and the CSR product fed by a TMA ring.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include "cg_internal.h"
 
@@ -516,11 +517,8 @@ __device__ __forceinline__ Acc seg_fma_n(const T* vp, int len, const X (&xv)[U],
   return s;
 }
 
-// Dispatch on the step's longest per-lane segment (1..32): one branch per step.
-#define CGK_SEG_CASES(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) \
-  M(16) M(17) M(18) M(19) M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32)
-
-#define CGK_SEG_CASES16(M) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)
+// The step's longest per-lane segment (1..32) selects the unrolled code once
+// per step (dispatch_tree below).
 
 // The multiply-adds of a lane's first 16 entries (xv holds their gathered
 // values), each followed by the gather of entry 16 + u into the register it
@@ -537,55 +535,40 @@ __device__ __forceinline__ Acc seg_fma_refill_n(const T* vp, const int32_t* cp2,
   return s;
 }
 
+// Calls f(std::integral_constant<int, v>) for v in [LO, HI] (values below LO
+// call f with LO) through a binary tree of warp-uniform conditional branches:
+// no indirect jump (a jump table's target must be resolved before the warp
+// can go on).
+template <int LO, int HI, typename F>
+__device__ __forceinline__ void dispatch_tree(int v, F&& f) {
+  if constexpr (LO == HI) {
+    f(std::integral_constant<int, LO>{});
+  } else {
+    constexpr int MID = (LO + HI) / 2;
+    if (v <= MID) dispatch_tree<LO, MID>(v, f);
+    else dispatch_tree<MID + 1, HI>(v, f);
+  }
+}
+
 template <typename T, typename X, typename Acc>
 __device__ __forceinline__ Acc seg_fma_refill(const T* vp, const int32_t* cp2, int len, int n2, const X* x,
                                               X (&xv)[16]) {
-  switch (n2) {
-#define CGK_R(N) case N: return seg_fma_refill_n<T, X, Acc, N>(vp, cp2, len, x, xv);
-    CGK_SEG_CASES16(CGK_R)
-#undef CGK_R
-    default: return Acc(0);
-  }
+  Acc s = Acc(0);
+  dispatch_tree<1, 16>(n2, [&](auto N) { s = seg_fma_refill_n<T, X, Acc, decltype(N)::value>(vp, cp2, len, x, xv); });
+  return s;
 }
 
 template <typename X, int U>
 __device__ __forceinline__ void seg_gather(const int32_t* cp, int len, int wmax, const X* x, X (&xv)[U]) {
   static_assert(U == 32 || U == 16, "dispatch covers 1..U");
-  if constexpr (U == 32) {
-    switch (wmax) {
-#define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
-      CGK_SEG_CASES(CGK_G)
-#undef CGK_G
-      default: break;
-    }
-  } else {
-    switch (wmax) {
-#define CGK_G(N) case N: seg_gather_n<X, N, U>(cp, len, x, xv); break;
-      CGK_SEG_CASES16(CGK_G)
-#undef CGK_G
-      default: break;
-    }
-  }
+  dispatch_tree<1, U>(wmax, [&](auto N) { seg_gather_n<X, decltype(N)::value, U>(cp, len, x, xv); });
 }
 
 template <typename T, typename X, typename Acc, int U>
 __device__ __forceinline__ Acc seg_fma(const T* vp, int len, int wmax, const X (&xv)[U], Acc s) {
   static_assert(U == 32 || U == 16, "dispatch covers 1..U");
-  if constexpr (U == 32) {
-    switch (wmax) {
-#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv, s);
-      CGK_SEG_CASES(CGK_F)
-#undef CGK_F
-      default: return s;
-    }
-  } else {
-    switch (wmax) {
-#define CGK_F(N) case N: return seg_fma_n<T, X, Acc, N, U>(vp, len, xv, s);
-      CGK_SEG_CASES16(CGK_F)
-#undef CGK_F
-      default: return s;
-    }
-  }
+  dispatch_tree<1, U>(wmax, [&](auto N) { s = seg_fma_n<T, X, Acc, decltype(N)::value, U>(vp, len, xv, s); });
+  return s;
 }
 
 // A segment longer than the unrolled capacity (up to kMirror entries: rows of
