@@ -14,10 +14,13 @@
  *   - Returns a cg_status code; nothing aborts and no C++ exception crosses
  *     the ABI.  cg_last_error() gives a message for the last failure.
  *   - "device" pointers are CUDA global-memory pointers of the handle's
- *     device (e.g. torch.Tensor.data_ptr() of a CUDA tensor).  They are
- *     borrowed: the library never frees or retains them after the call.
- *   - Work is queued on the handle's stream (cg_opts.stream); functions that
- *     produce a host-visible result (cg_solve) synchronise that stream.
+ *     device, or of the current device for the calls without a handle
+ *     (e.g. torch.Tensor.data_ptr() of a CUDA tensor).  They are borrowed:
+ *     the library never frees or retains them after the call.
+ *   - Work of a handle is queued on the handle's stream (cg_opts.stream);
+ *     the vector calls without a handle take their stream as an argument.
+ *     Functions that produce a host-visible result (cg_solve, cg_dot_host)
+ *     synchronise their stream.
  *   - Sizes are int64_t; the CSR arrays use int32_t indices, so n and nnz
  *     must each stay below 2^31 - 16.
  */
@@ -286,7 +289,9 @@ int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status);
  * copied to the request's x and its memory released before the next round.
  *
  * The arithmetic of every system is that of cg_solve with the batch's
- * precision (x0 = 0; the same stopping test and outputs).  How many CTAs
+ * precision (x0 = 0; the same stopping test and outputs; the product's step
+ * shapes, and so the split of a row's sum, follow the batch object's table,
+ * see cg_batch_opts.autotune and step_shape).  How many CTAs
  * solve a system (its "group") is chosen from the system alone (its rows,
  * entries and row lengths), never from the rest of the batch, so a system
  * gives the same bits alone and in any mix on the same batch object.  The
