@@ -382,6 +382,12 @@ typedef struct {
    * 64 entries always take a warp each. */
   int32_t shape_tuned;             /* 1 if the step shapes were measured */
   int32_t step_kind[6];
+  int32_t pad;
+  /* rounds whose product loaded the row pointers with the evict-first L2
+   * policy: those whose systems' vectors and row pointers together take
+   * more than 4/7 of the L2 (the row pointers then give way to the vectors
+   * that every step reads again) */
+  int64_t rounds_stream_rows;
 } cg_batch_stats;
 
 /* Fill *o with the defaults above. */

@@ -72,7 +72,8 @@ class cg_batch_stats(ctypes.Structure):
                 ("last_round_ms", ctypes.c_double), ("cta_bytes_per_s", ctypes.c_double),
                 ("group_cta_bytes_per_s", ctypes.c_double), ("step_overhead_s", ctypes.c_double),
                 ("group_step_overhead_s", ctypes.c_double), ("autotuned", ctypes.c_int32),
-                ("shape_tuned", ctypes.c_int32), ("step_kind", ctypes.c_int32 * 6)]
+                ("shape_tuned", ctypes.c_int32), ("step_kind", ctypes.c_int32 * 6), ("pad", ctypes.c_int32),
+                ("rounds_stream_rows", ctypes.c_int64)]
 
 
 def _load() -> ctypes.CDLL:
@@ -520,6 +521,7 @@ class Batch:
         self._check(lib.cg_batch_get_stats(self._b, ctypes.byref(s)))
         out = {f: getattr(s, f) for f, _ in cg_batch_stats._fields_}
         out["step_kind"] = list(s.step_kind)
+        out.pop("pad")
         return out
 
     def group_for(self, row_ptr) -> int:

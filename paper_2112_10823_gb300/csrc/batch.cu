@@ -218,6 +218,7 @@ struct cg_batch_ctx {
   bool validate = true;
   int nblocks = 0;
   int task_cap = 0;
+  int64_t l2_bytes = 0;       // the device's L2 (row-pointer policy of a round)
   GroupModel model;
   std::chrono::steady_clock::time_point t0;
 
@@ -249,6 +250,7 @@ struct cg_batch_ctx {
   std::vector<int> free_slots;
   std::vector<Job*> resident;
   int64_t rounds = 0, submitted = 0, admitted = 0, completed = 0;
+  int64_t rounds_stream_rows = 0;  // rounds whose product loaded the row pointers evict-first
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around each round, on the compute stream
   double round_ms_total = 0.0, last_round_ms = 0.0;
   std::string err;
@@ -590,47 +592,59 @@ void admit(cg_batch_ctx* b) {
   }
 }
 
-// Build the task queue of a round: the ranks of every group of several CTAs
-// first (largest remaining work first), then one-CTA systems, largest
-// remaining work first.  Returns the systems of the round.
+// Build the task queue of a round: the tasks of every resident system (the
+// ranks of a group next to each other), the longest estimated remaining
+// time per CTA first.  CTAs take the next entry as they free up, so this is
+// list scheduling in the longest-processing-time order: the round ends close
+// to the total work over the grid, with the short tasks filling the tail.
+// Returns the systems of the round.
 //
-// CTAs take entries in queue order, so a group whose ranks do not all fit in
-// the first wave is completed by CTAs that finish earlier group tasks; its
-// first ranks wait at their first group barrier meanwhile.  This cannot
-// deadlock: take the first group in queue order with an entry not yet taken;
-// every entry before it has been taken, no entry after it has, so every busy
-// CTA outside that group runs a task that can finish (a one-CTA task or a
-// group whose ranks are all running), and each group has at most as many
-// ranks as the grid has CTAs.  Since groups precede one-CTA tasks, such waits
-// last at most as long as a group task.
+// A group's ranks are taken as CTAs free up; its first ranks wait at their
+// first group barrier meanwhile.  This cannot deadlock: take the first group
+// in queue order with an entry not yet taken; every entry before it has been
+// taken, no entry after it has, so every busy CTA outside that group runs a
+// task that can finish (a one-CTA task or a group whose ranks are all
+// running), and each group has at most as many ranks as the grid has CTAs.
+// Such a wait lasts at most as long as the tasks ahead of the group in the
+// queue, which the order makes no shorter than the group's own.
 std::vector<Job*> build_queue(cg_batch_ctx* b, const std::vector<Job*>& res) {
-  std::vector<Job*> groups, singles;
-  for (Job* j : res) (j->group > 1 ? groups : singles).push_back(j);
+  const GroupModel& m = b->model;
   auto remaining = [&](const Job* j) {
     const double left = std::max(1.0, j->steps_est - static_cast<double>(j->res.iters));
     const double steps = b->chunk_iters > 0 ? std::min(left, static_cast<double>(b->chunk_iters)) : left;
-    return steps * j->bytes_step / j->group;
+    const double per_step = j->group > 1 ? j->bytes_step / (j->group * m.group_rate) + m.overhead_g
+                                         : j->bytes_step / m.cta_rate + m.overhead_1;
+    return steps * per_step;
   };
-  auto by_work = [&](const Job* a, const Job* c) {
-    const double wa = remaining(a), wc = remaining(c);
-    return wa != wc ? wa > wc : a->ticket < c->ticket;
-  };
-  std::sort(groups.begin(), groups.end(), by_work);
-  std::sort(singles.begin(), singles.end(), by_work);
+  std::vector<std::pair<double, Job*>> order;
+  order.reserve(res.size());
+  int singles = 0;
+  for (Job* j : res) {
+    order.emplace_back(remaining(j), j);
+    singles += j->group > 1 ? 0 : 1;
+  }
+  std::sort(order.begin(), order.end(), [](const std::pair<double, Job*>& a, const std::pair<double, Job*>& c) {
+    return a.first != c.first ? a.first > c.first : a.second->ticket < c.second->ticket;
+  });
   std::vector<Job*> in_round;
   int nt = 0;
-  int room = b->task_cap - static_cast<int>(singles.size());
-  for (Job* j : groups) {
-    if (j->group > room) continue;  // the queue is full: next round
-    room -= j->group;
-    for (int rk = 0; rk < j->group; ++rk) b->h_queue->task[nt++] = cgk::BatchTask{j->slot, rk};
-    in_round.push_back(j);
-  }
-  for (Job* j : singles) {
-    b->h_queue->task[nt++] = cgk::BatchTask{j->slot, 0};
+  int room = b->task_cap - singles;
+  for (const auto& e : order) {
+    Job* j = e.second;
+    if (j->group > 1) {
+      if (j->group > room) continue;  // the queue is full: next round
+      room -= j->group;
+      for (int rk = 0; rk < j->group; ++rk) b->h_queue->task[nt++] = cgk::BatchTask{j->slot, rk};
+    } else {
+      b->h_queue->task[nt++] = cgk::BatchTask{j->slot, 0};
+    }
     in_round.push_back(j);
   }
   b->h_queue->ntasks = nt;
+  // the systems of a round run side by side: their vectors share the L2
+  int64_t reused = 0;
+  for (const Job* j : in_round) reused += cgk::step_reused_bytes(j->req.n, b->mixed, b->jacobi);
+  b->h_queue->stream_rows = cgk::stream_row_ptrs(reused, b->l2_bytes) ? 1 : 0;
   return in_round;
 }
 
@@ -715,6 +729,7 @@ void worker_main(cg_batch_ctx* b) {
       {
         std::lock_guard<std::mutex> lk(b->mu);
         ++b->rounds;
+        if (b->h_queue->stream_rows) ++b->rounds_stream_rows;
         b->last_round_ms = ms;
         b->round_ms_total += ms;
       }
@@ -1029,6 +1044,12 @@ int cg_batch_create(cg_batch* out, const cg_batch_opts* opts) {
     return bfail(nullptr, CG_ECUDA, "cg_batch_create: the batch kernel cannot be resident");
   }
   b->nblocks = sms * per_sm;
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) != cudaSuccess) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  b->l2_bytes = l2;
   b->model.cta_rate = 6.7e12 / b->nblocks;
   // queue capacity: every resident system once, plus the extra ranks of
   // groups (a round whose groups need more is split over rounds)
@@ -1194,6 +1215,8 @@ int cg_batch_get_stats(cg_batch b, cg_batch_stats* st) {
   st->autotuned = b->autotuned ? 1 : 0;
   st->shape_tuned = b->shape_tuned ? 1 : 0;
   for (int k = 0; k < kShapeBuckets; ++k) st->step_kind[k] = b->shape.mode[kShapeHi[k]];
+  st->pad = 0;
+  st->rounds_stream_rows = b->rounds_stream_rows;
   return CG_OK;
 }
 

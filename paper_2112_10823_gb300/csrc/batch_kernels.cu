@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __gr
     stream_setup(sm, cs, P.A, tk.rank, reinit);
     reinit = true;
     if (threadIdx.x >= kConsumers) solve_producer<kMixed>(sm, cs, P);
-    else solve_consumers<kMixed, kJacobi, false, false>(sm, cs, P, tk.rank);
+    else solve_consumers<kMixed, kJacobi, false, false>(sm, cs, P, tk.rank, &B.queue->stream_rows);
     __syncthreads();  // producer drained, consumers done: the CTA is free
   }
 }

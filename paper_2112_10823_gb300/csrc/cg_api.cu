@@ -275,6 +275,18 @@ int sm_count(int dev) {
   return cache[dev];
 }
 
+int64_t l2_bytes(int dev) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  if (dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev] && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+    cudaGetLastError();
+    cache[dev] = 0;
+  }
+  return cache[dev];
+}
+
 cudaError_t blas_scratch(cudaStream_t s, int* dev_out, BlasScratch* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -728,7 +740,8 @@ int cg_solve(cg_handle h, const double* b, double* x, double tol, int64_t maxit,
   P.replace_every = h->replace_every;
   P.wait_limit_ns = h->wait_limit_ns;
   P.group = h->nblocks;
-  P.pad = 0;
+  P.stream_rows = cgk::stream_row_ptrs(
+      cgk::step_reused_bytes(h->n, h->precision == CG_PREC_MIXED, h->d_dinv != nullptr), l2_bytes(h->device));
   P.chunk_iters = 0;
   P.dinv = h->d_dinv;
   P.flags = h->nblocks > 1 ? h->d_flags : nullptr;

@@ -591,22 +591,33 @@ __device__ __forceinline__ Acc seg_dot_loop(const T* vp, const int32_t* cp, int 
 
 // Lane-private part of a lane-per-row or pair-per-row step.  The row
 // pointers are loaded when a step is two steps ahead and only consumed one
-// step later, so their latency stays off the critical path.
+// step later, so their latency stays off the critical path.  *stream != 0:
+// load them with the evict-first policy (__ldcs), so that in a solve whose
+// vectors and row pointers together outgrow the L2 the row pointers, read
+// once per product, give way to the vectors that the step reads again.  The
+// flag is read where it is used (a kernel parameter or an L1 hit) rather
+// than held in a register through the product.
 struct LaneRaw {
   int row;   // row whose (partial) sum this lane computes, -1 if none
   int ks;    // row_ptr[row]
   int ke;    // row_ptr[row + 1]
 };
 
-__device__ __forceinline__ LaneRaw lane_raw(const int32_t* row_ptr, int4 d, int mode, bool valid) {
+__device__ __forceinline__ LaneRaw lane_raw(const int32_t* row_ptr, int4 d, int mode, bool valid,
+                                            const int32_t* stream) {
   const int lane = threadIdx.x & 31;
   LaneRaw r{-1, 0, 0};
   if (valid && mode != kLongRow) {
     const int i = d.x + (mode == kLanePerRow ? lane : (lane >> 1));
     if (i < d.y) {
       r.row = i;
-      r.ks = row_ptr[i];
-      r.ke = row_ptr[i + 1];
+      if (*stream) {
+        r.ks = __ldcs(row_ptr + i);
+        r.ke = __ldcs(row_ptr + i + 1);
+      } else {
+        r.ks = row_ptr[i];
+        r.ke = row_ptr[i + 1];
+      }
     }
   }
   return r;
@@ -636,12 +647,13 @@ __device__ __forceinline__ void lane_span(const LaneRaw& r, int mode, int& a, in
 // releases pieces on the empty barriers once its next step starts beyond
 // them); otherwise entries are read directly from global memory (values
 // `val`, column indices A.col_idx).  Step descriptors are loaded two steps
-// ahead, row pointers and aux values one step ahead.  Returns false
+// ahead, row pointers and aux values one step ahead; *stream_rows != 0: row
+// pointers with the evict-first policy (lane_raw).  Returns false
 // (uniformly over the warp) if a wait gave up.
 template <bool kRingPass, typename T, typename X, typename Acc, typename Epi>
 __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& cs, ConsumerCursor& cur,
                                           const DevCsr& A, const T* val, const X* x, const double* aux, Epi& epi,
-                                          unsigned long long limit_ns) {
+                                          unsigned long long limit_ns, const int32_t* stream_rows) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* rv = kRingPass ? sm.val<T>() : val;
   const int32_t* rc = kRingPass ? sm.col() : A.col_idx;
@@ -671,14 +683,14 @@ __device__ __forceinline__ bool spmv_pass(const RingSmem& sm, const CtaStream& c
   int s = cs.s0 + w;
   int4 d0 = A.step[sd(s)], d1 = A.step[sd(s + kStride)];
   int m0 = A.step_mode[sd(s)], m1 = A.step_mode[sd(s + kStride)];
-  LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < cs.s1);
+  LaneRaw r0 = lane_raw(row_ptr, d0, m0 & 3, s < cs.s1, stream_rows);
   double a0 = (aux != nullptr && s < cs.s1 && holds_result(m0 & 3, r0)) ? aux[r0.row] : 0.0;
   for (; s < cs.s1; s += kStride) {
     const bool has1 = s + kStride < cs.s1;
     // prefetch: descriptor two steps ahead, row pointers and aux value of the next step
     const int4 d2 = A.step[sd(s + 2 * kStride)];
     const int m2 = A.step_mode[sd(s + 2 * kStride)];
-    const LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, has1);
+    const LaneRaw r1 = lane_raw(row_ptr, d1, m1 & 3, has1, stream_rows);
     const double a1 = (aux != nullptr && has1 && holds_result(m1 & 3, r1)) ? aux[r1.row] : 0.0;
     const int mode = m0 & 3;
     if (kRingPass && d0.w > d0.z) {

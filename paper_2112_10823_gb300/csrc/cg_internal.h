@@ -113,7 +113,7 @@ struct SolveParams {
   int64_t replace_every;        // mixed precision: true-residual period
   unsigned long long wait_limit_ns;  // bound on every device-side wait
   int32_t group;                // CTAs that solve this system together (its partition's CTA count)
-  int32_t pad;
+  int32_t stream_rows;          // single-system kernels: row pointers evict-first (stream_row_ptrs)
   int64_t chunk_iters;          // steps per launch (<= 0: until the solve ends)
   const double* dinv;           // Jacobi preconditioner 1/diag(A), or nullptr (plain CG)
   // Single-system solves: one epoch flag per CTA (zeroed before the launch).
@@ -132,7 +132,7 @@ struct BatchTask {
 };
 struct BatchQueue {
   int32_t ntasks;
-  int32_t pad;
+  int32_t stream_rows;          // row pointers evict-first in this launch (stream_row_ptrs)
   BatchTask task[1];            // ntasks entries (allocated to capacity)
 };
 struct BatchParams {
@@ -140,6 +140,26 @@ struct BatchParams {
   const BatchQueue* queue;      // tasks of this launch, group tasks first
   int32_t* next;                // next task to take (zeroed before each launch)
 };
+
+// Bytes that a step of the CG iteration on n rows reads again in the next
+// step: p, q and r, the row pointers, the FP32 copy of p (mixed precision)
+// and 1/diag(A) (Jacobi).  x and the matrix stream through with the
+// evict-first policy.
+inline int64_t step_reused_bytes(int64_t n, bool mixed, bool jacobi) {
+  return n * (28 + (mixed ? 4 : 0) + (jacobi ? 8 : 0));
+}
+
+// Whether the product loads the row pointers with the evict-first policy:
+// when the bytes that the running steps read again take more than 4/7 of
+// the L2.  Below that, row pointers and vectors both stay in the L2 from
+// step to step; above it the row pointers, read once per product, are the
+// better ones to give up.  On GB300 with the Q1 systems: 128^3 was 5.7 %
+// (mixed 3.5 %) and 136^3 0.5 % slower with them streamed; 136^3 mixed,
+// 144^3 and larger 0.3 to 1.8 % faster, and a batch of 256 systems of 8^3
+// to 48^3 4.5 % (mixed 8.9 %).
+inline bool stream_row_ptrs(int64_t reused_bytes, int64_t l2_bytes) {
+  return l2_bytes > 0 && 7 * reused_bytes > 4 * l2_bytes;
+}
 
 // Status codes (same values as include/cg.h).
 enum : int32_t {

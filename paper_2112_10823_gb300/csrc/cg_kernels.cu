@@ -33,7 +33,7 @@ namespace cgk {
 // One system on the whole grid: CTA c is rank c of the group.  kJacobi:
 // preconditioned by M = diag(A) (P.dinv).
 template <bool kMixed, bool kJacobi, bool kSmallShare>
-__global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const SolveParams P) {
+__global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const __grid_constant__ SolveParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const RingSmem sm{smem_raw, kMixed ? 4u : 8u};  // the step loop streams FP32 values in the mixed solve
   CtaStream cs;
@@ -44,8 +44,11 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_solve_kernel(const Solv
   }
   // the neighbour wait at the end of a step pays off on large shares (160^3:
   // 1.6 % faster); on small ones the group barrier is faster (64^3: 1 %, 16^3: 9 %)
-  solve_consumers<kMixed, kJacobi, kSmallShare, !kSmallShare>(sm, cs, P, blockIdx.x);
+  solve_consumers<kMixed, kJacobi, kSmallShare, !kSmallShare>(sm, cs, P, blockIdx.x, &P.stream_rows);
 }
+
+// The product alone reads every row pointer once: always evict-first.
+__constant__ int32_t kStreamRowsAlways = 1;
 
 // y = A x (same partition and stream as the solve; one pass).
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A, const double* __restrict__ x,
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm) spmv_kernel(const DevCsr A
   }
   ConsumerCursor cur;
   auto epi = [&](int i, double s, double) { y[i] = s; };
-  const bool ok = cta_and(spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, x, nullptr, epi, lim));
+  const bool ok = cta_and(spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, x, nullptr, epi, lim, &kStreamRowsAlways));
   if (!ok && threadIdx.x == 0) atomicExch(err, kETIMEOUT);
   consumers_done(sm);
 }

@@ -70,7 +70,7 @@ __host__ __device__ constexpr int vec_rows() {
 // registers of the step loop's product are the product's own.
 template <bool kMixed, bool kJacobi, bool kSmallShare, bool kNeighborWait>
 __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStream& cs, const SolveParams& P,
-                                                const int rank) {
+                                                const int rank, const int32_t* stream_rows) {
   // kNeighborWait: the single-system kernel for large shares (P.flags set
   // when the group has several CTAs); the small-share and batched kernels
   // always use the group barrier.
@@ -220,7 +220,7 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
   // product out of them leaves its single copy, in the step loop, the
   // registers it needs.  The ring keeps streaming what the step loop uses.
   auto product64 = [&](const double* xin, const double* aux, auto& epi) -> bool {
-    return spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, P.wait_limit_ns);
+    return spmv_pass<false, double, double, double>(sm, cs, cur, A, A.val, xin, aux, epi, P.wait_limit_ns, stream_rows);
   };
 
   // ---- state: saved by an earlier launch of this solve (written by another
@@ -341,13 +341,15 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
         P.q[i] = qi;
         acc_g = fma(pi, qi, acc_g);
       };
-      ok = spmv_pass<true, float, float, float>(sm, cs, cur, A, A.val32, P.p32, p, epi, P.wait_limit_ns);
+      ok = spmv_pass<true, float, float, float>(sm, cs, cur, A, A.val32, P.p32, p, epi, P.wait_limit_ns,
+                                                  stream_rows);
     } else {
       auto epi = [&](int i, double s, double pi) {
         P.q[i] = s;
         acc_g = fma(pi, s, acc_g);
       };
-      ok = spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, p, p, epi, P.wait_limit_ns);
+      ok = spmv_pass<true, double, double, double>(sm, cs, cur, A, A.val, p, p, epi, P.wait_limit_ns,
+                                                     stream_rows);
     }
     // alpha = rho / gamma, once per CTA (an FP64 division is slow)
     if (!group_sum(ok, 1, acc_g, 0.0, 0.0, [&](const double* sum) {
@@ -498,14 +500,14 @@ __device__ __forceinline__ void solve_consumers(const RingSmem& sm, const CtaStr
             pv[u] = p[i];
             zv[u] = R(i);
             if constexpr (kJacobi) zv[u] = P.dinv[i] * zv[u];
-            xv[u] = x[i];
+            xv[u] = __ldcs(x + i);  // x is not read again this step: evict-first
           }
         }
 #pragma unroll
         for (int u = 0; u < kVR; ++u) {
           const int i = base + u * kConsumers;
           if (i < row1) {
-            x[i] = fma(alpha, pv[u], xv[u]);
+            __stcs(x + i, fma(alpha, pv[u], xv[u]));
             const double pn = fma(beta, pv[u], zv[u]);
             p[i] = pn;
             if constexpr (kMixed) P.p32[i] = static_cast<float>(pn);

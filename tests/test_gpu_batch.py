@@ -77,6 +77,8 @@ def test_batch_matches_oracle_per_system():
         results = _wait_all(bt, tickets)
         st = bt.stats()
     assert st["graph"] == 1, "rounds should replay a captured CUDA graph"
+    # a few kB of vectors: the row pointers keep the default L2 policy
+    assert st["rounds_stream_rows"] == 0
     for (A, b), req, res in zip(systems, reqs, results):
         assert res.tag == req.tag
         _check_vs_oracle(A, b, res, _x(req))
@@ -246,6 +248,13 @@ def test_batch_of_256_uneven_systems_sampled():
         st = bt.stats()
     assert st["completed"] == 256
     assert all(r.status == cg.CG_OK and r.relres <= TOL for r in res)
+    # p, q, r (FP64), the FP32 copy of p and the row pointers of the systems
+    # of a round outgrow 4/7 of the L2: the row pointers are streamed
+    import torch
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    if 7 * 32 * sum(A.n for A, _ in systems) > 4 * l2:
+        assert st["rounds_stream_rows"] >= 1, st
+    assert st["rounds_stream_rows"] <= st["rounds"]
     for i in range(0, 256, 37):
         A, b = systems[i]
         x = _x(reqs[i])
