@@ -870,14 +870,14 @@ def run_variants(args, cg, A, xs, x64, dev, stream, energy, hbm, fp64, fp64_line
     torch.cuda.empty_cache()
     # the configured stream (2000 requests/s, beyond one GPU's capacity: the
     # sustained rate and the latency under overload) over a quarter second,
-    # and a lighter one (100 requests/s) with groups sized for 10 ms solo
-    # solves, for latency below capacity
+    # and a lighter one (100 requests/s) configured for latency below
+    # capacity: groups sized for 5 ms solo solves, rounds of 20 steps
     guarded("serve_2000rps_mixed", lambda: serve_record(cg, args.seed, 2000.0, 0.25, dev, stream, energy, hbm[0],
                                                        "mixed", "none", budget_gb=args.budget_gb, chunk=args.chunk,
                                                        autotune=True, group_target_ms=args.group_target_ms))
-    guarded("serve_100rps_mixed_10ms", lambda: serve_record(cg, args.seed + 1, 100.0, 1.0, dev, stream, energy,
-                                                           hbm[0], "mixed", "none", budget_gb=args.budget_gb,
-                                                           chunk=args.chunk, autotune=True, group_target_ms=10))
+    guarded("serve_100rps_mixed_5ms", lambda: serve_record(cg, args.seed + 1, 100.0, 1.0, dev, stream, energy,
+                                                          hbm[0], "mixed", "none", budget_gb=args.budget_gb,
+                                                          chunk=20, autotune=True, group_target_ms=5))
     return out
 
 

@@ -297,7 +297,9 @@ int cg_selftest_wait_timeout(int32_t limit_ms, int32_t* kernel_status);
  * gives the same bits alone and in any mix on the same batch object.  The
  * choice is the smallest group whose estimated solo solve time meets
  * group_target_ms under a cost model (per-CTA streaming rate and per-step overheads) that
- * cg_batch_opts.autotune measures on the GPU at creation.
+ * cg_batch_opts.autotune measures on the GPU at creation; a group has at most half the
+ * CTAs of the persistent grid and at least 1024 rows per CTA, and when no group meets the
+ * target the largest one is taken.
  * ---------------------------------------------------------------------- */
 
 typedef struct cg_batch_ctx* cg_batch;

