@@ -325,7 +325,10 @@ typedef struct {
                               synthetic systems (about a second of rounds); 0 (default):
                               built-in shapes and constants */
   int32_t group_target_ms; /* solo solve time the automatic group size aims at (default 50:
-                              smaller favours latency, larger favours throughput) */
+                              smaller favours latency, larger favours throughput).  Keep it
+                              well below wait_limit_ms when chunk_iters is 0: the first
+                              ranks of a group may wait at their first barrier for about
+                              one task (up to one solo solve) to end */
   int32_t step_shape;      /* 0 (default): the built-in step shapes, or the measured ones with
                               autotune; 1: the built-in shapes (one lane per row up to 32
                               entries, two lanes up to 64) even with autotune; 2: two lanes per
