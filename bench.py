@@ -860,7 +860,8 @@ def run_variants(args, cg, A, xs, x64, dev, stream, energy, hbm, fp64, fp64_line
         if not systems:
             systems.extend(batch_systems(args.seed, args.batch_count, dev))
         return batch_record(cg, systems, dev, stream, energy, hbm[0], precision, "none", steps=3, warmup=1,
-                            budget_gb=32.0, autotune=True, group_target_ms=args.group_target_ms)
+                            budget_gb=32.0, autotune=True, group_target_ms=args.group_target_ms,
+                            traffic_key=f"batch{args.batch_count}_seed{args.seed}_{precision}")
 
     guarded("batch256_fp64", lambda: batch("fp64"))
     guarded("batch256_mixed", lambda: batch("mixed"))
@@ -924,9 +925,11 @@ def solve_sequential(systems, stream):
 
 
 def batch_record(cg, systems, dev, stream, energy, hbm_peak, precision, precond, steps, warmup, budget_gb,
-                 autotune, group_target_ms, e2e=False):
+                 autotune, group_target_ms, e2e=False, traffic_key=None):
     """The batch per step in one persistent launch (batched API), against the
-    same systems solved one after another by cg_solve in FP64."""
+    same systems solved one after another by cg_solve in FP64.  traffic_key
+    names the workload's line in the ncu traffic record (DRAM bytes of one
+    whole batch, every round of it), if it has one."""
     import torch
     count = len(systems)
     mixed = precision == "mixed"
@@ -986,6 +989,7 @@ def batch_record(cg, systems, dev, stream, energy, hbm_peak, precision, precond,
     bytes_batch = sum(solve_bytes(s["n"], s["nnz"], it, mixed, jacobi=jac) for s, it in zip(systems, iters))
     flops_batch = sum(solve_flops(s["n"], s["nnz"], it, mixed, jacobi=jac) for s, it in zip(systems, iters))
     achieved = bytes_batch * steps / dev_s / 1e9
+    kernel = f"cg_batch_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>"
     rec = {
         "value": value, "unit": "solves/s", "ms_per_batch": 1000.0 * dev_s / steps, "steps": steps,
         "dtype": "f32+f64" if mixed else "f64",
@@ -997,8 +1001,11 @@ def batch_record(cg, systems, dev, stream, energy, hbm_peak, precision, precond,
         "groups": {str(g): groups.count(g) for g in sorted(set(groups))},
         "rounds_per_step": rounds / steps, "graph": bool(st1["graph"]), "group_model": model,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": f"cg_batch_kernel<{'true' if mixed else 'false'}, {'true' if jac else 'false'}>",
+                     "frac": achieved / hbm_peak,
+                     "traffic": recorded_traffic(kernel, traffic_key) if traffic_key else None,
+                     "traffic_per": "batch (the DRAM bytes of all rounds of one batch)",
+                     "algorithmic_bytes_per_batch": bytes_batch,
+                     "kernel": kernel,
                      "gflops": flops_batch * steps / dev_s / 1e9},
         "accuracy": {"max_relres_true": max(r.relres for r in res), "max_rel_diff_vs_fp64_cg_solve": err},
         "fp64_sequential": seq,
@@ -1192,7 +1199,9 @@ def run_batch(args):
     systems = batch_systems(args.seed, args.batch_count, dev)
     hbm_peak, _ = peaks()
     rec = batch_record(cg, systems, dev, stream, Energy(0), hbm_peak, args.precision, args.precond, args.steps,
-                       args.warmup, args.budget_gb, not args.no_autotune, args.group_target_ms, e2e=True)
+                       args.warmup, args.budget_gb, not args.no_autotune, args.group_target_ms, e2e=True,
+                       traffic_key=(f"batch{args.batch_count}_seed{args.seed}_{args.precision}"
+                                    if args.precond == "none" else None))
     line = {"metric": METRIC, "value": rec["value"], "unit": "solves/s", "n_gpus": 1, "steps": rec["steps"],
             "warmup": args.warmup, "ms_per_step": rec["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
