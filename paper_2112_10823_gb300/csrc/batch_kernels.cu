@@ -7,11 +7,12 @@
 namespace cgk {
 
 // Many systems in one persistent launch: each CTA takes tasks (a system and
-// its rank in the system's group) from the queue until it is empty.  Group
-// tasks come first in the queue and all fit in the grid, so the ranks of a
-// group start together; the rest are one-CTA tasks, taken in queue order as
-// CTAs free up.  Between tasks the whole CTA (producer included) joins, the
-// producer having drained its copies, and the ring barriers are reset.
+// its rank in the system's group) from the queue, in queue order, until it is
+// empty.  The host orders the queue longest estimated time per CTA first,
+// with a group's ranks next to each other; a group's first ranks wait at its
+// first group barrier until CTAs that free up have taken the rest.  Between
+// tasks the whole CTA (producer included) joins, the producer having drained
+// its copies, and the ring barriers are reset.
 template <bool kMixed, bool kJacobi>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm) cg_batch_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];

@@ -137,7 +137,7 @@ struct BatchQueue {
 };
 struct BatchParams {
   const SolveParams* sys;       // system table (one entry per slot)
-  const BatchQueue* queue;      // tasks of this launch, group tasks first
+  const BatchQueue* queue;      // tasks of this launch, longest time per CTA first
   int32_t* next;                // next task to take (zeroed before each launch)
 };
 
