@@ -4,7 +4,6 @@ import os
 import re
 import subprocess
 
-import numpy as np
 import pytest
 
 import fe_inputs as fi

@@ -1,5 +1,4 @@
 """The seeded input generator: structure of the operators and the random streams (CPU only)."""
-import math
 
 import numpy as np
 

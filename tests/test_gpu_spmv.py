@@ -4,7 +4,7 @@ import pytest
 
 import fe_inputs as fi
 import oracle
-from gpu_util import abs_scale, cg_mod, dev_csr, handle, spmv_tol
+from gpu_util import cg_mod, dev_csr, handle, spmv_tol
 from pins import load_paper_example
 
 pytestmark = pytest.mark.gpu
