@@ -380,7 +380,9 @@ def pin_pcg_jacobi():
     (3) A constant diagonal (the 7-point operator, diagonal 6) makes the
         preconditioner a multiple of the identity: the iterates are CG's.
     (4) The inverse diagonal is the reciprocal of the brute-force diagonal;
-        a non-positive diagonal is refused (breakdown)."""
+        a non-positive diagonal is refused (breakdown).
+    (5) The stopping test is on the unpreconditioned residual: with a large
+        diagonal the stop is the first step with ||b - A x|| <= tol ||b||."""
     A = fi.q1(5, sigma=1.0, seed=31)
     D = A.to_dense()
     d = np.diag(D).copy()
@@ -408,6 +410,17 @@ def pin_pcg_jacobi():
     rp, rc = oracle.pcg_jacobi(L, bl, tol=1e-10, maxit=1000), oracle.cg(L, bl, tol=1e-10, maxit=1000)
     assert abs(rp.iters - rc.iters) <= 1
     assert np.linalg.norm(rp.x - rc.x) <= 1e-9 * np.linalg.norm(rc.x)
+    # (5) the stopping test is on the unpreconditioned residual: on a system
+    # whose diagonal is large (z = r / 6000) the solve stops at the first
+    # step whose ||b - A x|| (recursive, and recomputed) is within tol ||b||
+    Lb = fi.laplace7(6)
+    Lb.val = Lb.val * 1000.0
+    bb = oracle.spmv(Lb, fi.xstar(33, Lb.n))
+    r = oracle.pcg_jacobi(Lb, bb, tol=1e-8, maxit=1000)
+    assert r.status == oracle.OK and r.relres_rec <= 1e-8 and r.relres_true <= 1.01e-8
+    prev = oracle.pcg_jacobi(Lb, bb, tol=0.0, maxit=r.iters - 1, force_iters=r.iters - 1)
+    res_prev = np.linalg.norm(bb - oracle.spmv(Lb, prev.x)) / np.linalg.norm(bb)
+    assert res_prev > 1e-8 * 0.99
     # (4)
     Bad = fi.dense_to_csr(np.array([[2.0, 0.5], [0.5, -1.0]]))
     assert oracle.jacobi_dinv(Bad) is None

@@ -59,6 +59,22 @@ MUTANTS = [
     ("jacobi_diag_from_first_entry", "if ((int64_t)JA[k] - base == i) d = d + AA[k];",
      "if (k == (int64_t)IA[i] - base) d = d + AA[k];"),
     ("stats_bandwidth_off_by_one", "int64_t d = (int64_t)(JA[k] - base) - i;", "int64_t d = (int64_t)(JA[k] - base) - i + 1;"),
+    ("cg_true_residual_sign",
+     "    for (int64_t i = 0; i < n; ++i) { double d = b[i] - q[i]; t = t + d * d; }\n"
+     "    *relres_true = sqrt(t) / bnorm;\n    free(r); free(p); free(q);\n    return status;",
+     "    for (int64_t i = 0; i < n; ++i) { double d = b[i] + q[i]; t = t + d * d; }\n"
+     "    *relres_true = sqrt(t) / bnorm;\n    free(r); free(p); free(q);\n    return status;"),
+    ("cg_ignores_initial_guess",
+     "for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }\n"
+     "    double rho = oracle_dot(n, r, r);\n    if (res_h && hist_len > 0) res_h[0] = sqrt(rho);",
+     "for (int64_t i = 0; i < n; ++i) { r[i] = b[i]; p[i] = r[i]; }\n"
+     "    double rho = oracle_dot(n, r, r);\n    if (res_h && hist_len > 0) res_h[0] = sqrt(rho);"),
+    ("pcg_setup_rho_uses_r_r", "double rho = oracle_dot(n, r, z);\n    double rr = oracle_dot(n, r, r);",
+     "double rho = oracle_dot(n, r, r);\n    double rr = oracle_dot(n, r, r);"),
+    ("pcg_stop_test_on_z", "rr = oracle_dot(n, r, r);\n        k = k + 1;\n        if (force_iters < 0 && sqrt(rr) <= tol * bnorm) { done = 1; break; }",
+     "rr = oracle_dot(n, z, z);\n        k = k + 1;\n        if (force_iters < 0 && sqrt(rr) <= tol * bnorm) { done = 1; break; }"),
+    ("mixed_fp32_product_summed_in_fp64", "float s = 0.0f;\n        for (int64_t k = (int64_t)IA[i] - base; k < (int64_t)IA[i + 1] - base; ++k)\n            s = s + AA32[k] * x32[JA[k] - base];",
+     "double s = 0.0;\n        for (int64_t k = (int64_t)IA[i] - base; k < (int64_t)IA[i + 1] - base; ++k)\n            s = s + (double)AA32[k] * (double)x32[JA[k] - base];"),
 ]
 
 
