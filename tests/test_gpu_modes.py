@@ -115,6 +115,80 @@ def test_large_share_kernel_neighbour_waits(kind):
     assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
 
 
+def _hub_matrix(N: int, seed: int):
+    """The 7-point operator on an N^3 grid with coupling rows of three kinds
+    added symmetrically: row 0 coupled to every other row (a row longer than
+    several ring pieces), row n/2 to every third row, 50 rows to 30 random
+    rows each and 50 rows to 70 (rows of about 40 and 80 entries: two-lane
+    and warp steps);
+    each added coupling is -0.01 and adds 0.01 to both diagonals, plus 0.05
+    on every diagonal (strictly diagonally dominant, hence SPD)."""
+    L = fi.laplace7(N)
+    n = L.n
+    rows = [dict(zip(L.col_idx[L.row_ptr[i]:L.row_ptr[i + 1]].tolist(),
+                     L.val[L.row_ptr[i]:L.row_ptr[i + 1]].tolist())) for i in range(n)]
+    rng = np.random.default_rng(seed)
+
+    def couple(i, j):
+        if i == j or j in rows[i]:
+            return
+        rows[i][j] = -0.01
+        rows[j][i] = -0.01
+        rows[i][i] += 0.01
+        rows[j][j] += 0.01
+
+    for j in range(1, n):
+        couple(0, j)
+    for j in range(0, n, 3):
+        couple(n // 2, j)
+    for i in range(100, 200):
+        for j in rng.choice(n, size=30 if i < 150 else 70, replace=False):
+            couple(i, int(j))
+    rp, ci, va = [0], [], []
+    for i in range(n):
+        rows[i][i] += 0.05
+        cols = sorted(rows[i])
+        ci.extend(cols)
+        va.extend(rows[i][c] for c in cols)
+        rp.append(len(ci))
+    return fi.CSR(np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), np.array(va), n)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_share_kernel_all_step_kinds(precision):
+    """The large-share kernel over two CTAs on rows of every step kind at
+    once (up to 9 entries, about 40, about 80, 2,670 and 8,000 entries: one
+    lane, two lanes, a warp per row, and rows spanning several 2,048-entry
+    ring pieces): in FP64 the oracle's iterate at the GPU's step count, in
+    mixed precision the FP64 solution within the residual's reach; the true
+    residual, and the same bits on a second solve."""
+    cg = cg_mod()
+    A = _hub_matrix(20, 71)
+    lens = np.diff(A.row_ptr)
+    assert lens.max() >= 8000 and ((lens > 32) & (lens <= 64)).any() and ((lens > 64) & (lens < 1000)).any()
+    b = oracle.spmv(A, fi.xstar(71, A.n))
+    mixed = precision == "mixed"
+    with handle(A, ctas=2, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64) as h:
+        assert h.partition_info()[1] == cg.CG_SOLVE_KERNEL_LARGE_SHARE
+        res, x = _solve(h, b)
+        res2, x2 = _solve(h, b)
+    assert res.status == cg.CG_OK and res.relres <= TOL, res
+    assert res2.iters == res.iters and np.array_equal(x, x2)
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1.0000001 * TOL * np.linalg.norm(b)
+    if mixed:
+        # a long row's FP32 sum is split over a warp's lanes, which rounds
+        # differently from the oracle's one FP32 chain per row, so the mixed
+        # run is held to the FP64 solution (as for the other irregular rows)
+        ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
+        kap = kappa_estimate(A, b)
+        assert np.linalg.norm(x - ref.x) <= 2.02 * kap * TOL * np.linalg.norm(ref.x)
+    else:
+        ref = oracle.cg(A, b, tol=TOL, maxit=20 * A.n)
+        assert iters_close(res.iters, ref.iters), (res.iters, ref.iters)
+        same = oracle.cg(A, b, tol=0.0, maxit=res.iters, force_iters=res.iters)
+        assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
+
+
 @pytest.mark.parametrize("variant", ["mixed", "jacobi", "mixed_jacobi"])
 def test_large_share_kernel_neighbour_waits_variants(variant):
     """The mixed-precision and Jacobi variants of the large-share kernel (the
