@@ -23,6 +23,9 @@
  *     synchronise their stream.
  *   - Sizes are int64_t; the CSR arrays use int32_t indices, so n and nnz
  *     must each stay below 2^31 - 16.
+ *   - Threads: a handle holds the work vectors of one solve, so calls on
+ *     one handle must not overlap (use one handle per thread); the calls
+ *     without a handle and the batch API may be used from any thread.
  */
 #ifndef CG_GB300_H
 #define CG_GB300_H
