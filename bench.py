@@ -841,6 +841,14 @@ def run_variants(args, cg, A, xs, x64, dev, stream, energy, hbm, fp64, fp64_line
         rec["spmv"] = {"gbs": gbs, "frac": gbs / hbm[0], "ms": ms, "bytes": spmv_bytes(A64.n, A64.nnz),
                        "l2": "flushed before every call (the 87.6 MB product barely exceeds L2)"}
         h.close()
+        # the three group-wide synchronisations of a small-share step (two
+        # sums, one barrier), timed alone on the whole grid
+        bar_us, sum_us = cg.cg_probe_group_sync(dev.index or 0, 20000)
+        step_us = 1000.0 * rec["ms_per_solve"] / rec["iters"]
+        rec["sync_probe"] = {"barrier_us": bar_us, "sum_us": sum_us, "per_step_us": 2 * sum_us + bar_us,
+                             "step_us": step_us, "share_of_step": (2 * sum_us + bar_us) / step_us,
+                             "source": "cg_probe_group_sync (the solves' group barrier and group sum, one CTA "
+                                       "per SM, 20000 of each)"}
         return rec
 
     guarded("q1_64_fp64", q1_64)

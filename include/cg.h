@@ -209,6 +209,21 @@ int cg_blas_release(void);
 int cg_probe_fp64_peak(int32_t device, double* gflops);
 
 /*
+ * The cost of the solves' group-wide synchronisations, measured on the
+ * device (no counterpart in the paper; it explains the time of a step that
+ * the FP64 pipe does not).  A cooperative launch of one CTA per SM, the
+ * solve kernels' block, runs `iters` group barriers (*barrier_us: the
+ * barrier a solve step ends with) and then `iters` group sums
+ * (*sum_us: a CTA value published, the barrier, the group's values summed
+ * exactly in fixed point, as for alpha and beta), each between CTA barriers
+ * as in a step; the results are microseconds per barrier and per sum (CUDA
+ * events, one warm-up launch first).  device < 0: the current device.
+ * iters in [1, 10^6] (2*10^4 takes about 0.1 s).  Returns CG_ETIMEOUT if a
+ * wait gave up (2 s), CG_EINVAL for bad arguments.
+ */
+int cg_probe_group_sync(int32_t device, int32_t iters, double* barrier_us, double* sum_us);
+
+/*
  * Solve A x = b by classical CG (Sec. 5.3; Hestenes-Stiefel form):
  *   r = b - A x0, p = r; each step q = A p, alpha = r.r / p.q,
  *   x += alpha p, r -= alpha q, beta = r'.r' / r.r, p = r' + beta p;

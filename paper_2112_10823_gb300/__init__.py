@@ -13,5 +13,5 @@ from ._binding import (  # noqa: F401
     CG_SOLVE_KERNEL_LARGE_SHARE, CG_SOLVE_KERNEL_SMALL_SHARE, LIB_PATH, Batch, BatchResult, CGError, Handle, Request, SolveResult, cg_axpy,
     cg_create,
     cg_blas_release, cg_destroy, cg_dot, cg_dot_host, cg_dot_noalloc, cg_ewmul, cg_probe_fp64_peak,
-    cg_selftest_wait_timeout, cg_solve, cg_spmv, last_error, lib,
+    cg_probe_group_sync, cg_selftest_wait_timeout, cg_solve, cg_spmv, last_error, lib,
 )

@@ -109,6 +109,8 @@ def _load() -> ctypes.CDLL:
     lib.cg_blas_release.argtypes = []
     lib.cg_probe_fp64_peak.restype = ctypes.c_int
     lib.cg_probe_fp64_peak.argtypes = [i32, P(dbl)]
+    lib.cg_probe_group_sync.restype = ctypes.c_int
+    lib.cg_probe_group_sync.argtypes = [i32, i32, P(dbl), P(dbl)]
     lib.cg_solve.restype = ctypes.c_int
     lib.cg_solve.argtypes = [vp, vp, vp, dbl, i64, P(i64), P(dbl)]
     lib.cg_dot_noalloc.restype = ctypes.c_int
@@ -364,6 +366,14 @@ def cg_probe_fp64_peak(device: int = -1) -> float:
     g = ctypes.c_double(0.0)
     _check(lib.cg_probe_fp64_peak(int(device), ctypes.byref(g)))
     return g.value
+
+
+def cg_probe_group_sync(device: int = -1, iters: int = 20000) -> tuple[float, float]:
+    """Measured cost of the solves' group barrier and group sum on the whole
+    grid: (microseconds per barrier, microseconds per sum)."""
+    bar, summ = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.cg_probe_group_sync(int(device), int(iters), ctypes.byref(bar), ctypes.byref(summ)))
+    return bar.value, summ.value
 
 
 def cg_solve(h: Handle, b, x, tol: float = 1e-10, maxit: int | None = None, raise_on_error: bool = False

@@ -685,6 +685,62 @@ int cg_probe_fp64_peak(int32_t device, double* gflops) {
   return CG_OK;
 }
 
+int cg_probe_group_sync(int32_t device, int32_t iters, double* barrier_us, double* sum_us) {
+  if (!barrier_us || !sum_us || iters < 1 || iters > 1000000)
+    return fail(nullptr, CG_EINVAL, "cg_probe_group_sync: iters in [1, 10^6] and two outputs");
+  *barrier_us = 0.0;
+  *sum_us = 0.0;
+  int dev = device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, CG_ECUDA, "cg_probe_group_sync: no device");
+  DeviceGuard g(dev);
+  const int sms = sm_count(dev);
+  if (sms <= 0) return fail(nullptr, CG_ECUDA, "cg_probe_group_sync: SM count");
+  const int nb = sms * cgk::kCtasPerSm;
+  char* buf = nullptr;
+  cgk::SolveCtrl* ctrl = nullptr;
+  double* partials = nullptr;
+  double* out = nullptr;
+  const size_t ctrl_bytes = (sizeof(cgk::SolveCtrl) + 255) & ~size_t(255);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&buf, ctrl_bytes + sizeof(double) * 3 * static_cast<size_t>(nb));
+  if (e == cudaSuccess) {
+    ctrl = reinterpret_cast<cgk::SolveCtrl*>(buf);
+    partials = reinterpret_cast<double*>(buf + ctrl_bytes);
+    out = partials + 2 * static_cast<size_t>(nb);
+    e = cudaEventCreate(&e0);
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  bool timed_out = false;
+  double per_iter[2] = {0.0, 0.0};
+  for (int mode = 0; e == cudaSuccess && mode < 2 && !timed_out; ++mode) {
+    // a short launch first (clocks, first-touch), then the timed one
+    for (int rep = 0; e == cudaSuccess && rep < 2; ++rep) {
+      const int n_it = rep == 0 ? std::max(1, iters / 10) : iters;
+      e = cudaMemset(ctrl, 0, sizeof(cgk::SolveCtrl));
+      if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+      if (e == cudaSuccess) e = cgk::launch_sync_probe(ctrl, partials, n_it, mode, nb, 2000000000ull, out, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      int32_t abort_flag = 0;
+      if (e == cudaSuccess)
+        e = cudaMemcpy(&abort_flag, &ctrl->abort, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && abort_flag) timed_out = true;
+      if (e == cudaSuccess && rep == 1) per_iter[mode] = 1000.0 * static_cast<double>(ms) / n_it;
+      if (timed_out) break;
+    }
+  }
+  if (e1) cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (buf) cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cg_probe_group_sync");
+  if (timed_out) return fail(nullptr, CG_ETIMEOUT, "cg_probe_group_sync: a group barrier wait gave up");
+  *barrier_us = per_iter[0];
+  *sum_us = per_iter[1];
+  return CG_OK;
+}
+
 int cg_blas_release(void) {
   std::lock_guard<std::mutex> lock(g_blas_mu);
   int cur = -1;

@@ -215,6 +215,14 @@ cudaError_t launch_cluster_solve(const int32_t* row_ptr, const int32_t* col_idx,
 constexpr int32_t kSelftestSite = 99;
 // timeout_site of a single-system solve's wait for its neighbours' p
 constexpr int32_t kNeighborSite = 98;
+// timeout_site of the synchronisation probe's barrier
+constexpr int32_t kProbeSite = 97;
+// The solves' group-wide synchronisations timed alone (cg_probe_group_sync):
+// a cooperative launch of `nblocks` CTAs (one per SM) running `iters` group
+// barriers (mode 0) or group sums (mode 1); ctrl zeroed before the launch,
+// partials 2 * nblocks doubles, out nblocks doubles.
+cudaError_t launch_sync_probe(SolveCtrl* ctrl, double* partials, int iters, int mode, int nblocks,
+                              unsigned long long limit_ns, double* out, cudaStream_t s);
 // Shared-memory bytes of a persistent solve CTA (FP32 ring values if mixed;
 // `local`: the small-share kernels, with r of the share).
 size_t solve_smem_bytes(bool mixed, bool local = false);

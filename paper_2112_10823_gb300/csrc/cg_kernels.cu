@@ -190,4 +190,58 @@ cudaError_t launch_wait_timeout_selftest(SolveCtrl* ctrl, unsigned long long lim
   return cudaGetLastError();
 }
 
+// ---- cost of the solves' group-wide synchronisations on the whole grid
+// (one CTA per SM, the solve kernel's block): `iters` times, between CTA
+// barriers as in a solve step, warp 0 of every CTA either meets the others at
+// the group barrier (mode 0: group_barrier_t0), or runs a group sum (mode 1:
+// publishes the CTA's value in one of two alternating slots, meets the others
+// at the barrier, and sums the group's values exactly with
+// fx_warp_sum_array, as group_sum in the solve does).  The waits are the
+// solves' bounded ones: a wait that gives up raises ctrl->abort, after which
+// every CTA stops.  out[rank] keeps the sums live.
+__global__ void __launch_bounds__(kBlock, kCtasPerSm)
+    sync_probe_kernel(SolveCtrl* ctrl, double* partials, int iters, int mode, unsigned long long limit_ns,
+                      double* out) {
+  __shared__ unsigned long long target;
+  __shared__ int ok;
+  __shared__ double total;
+  const int nb = static_cast<int>(gridDim.x), rank = static_cast<int>(blockIdx.x);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    target = 0;
+    ok = 1;
+    total = 0.0;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = 0; k < iters; ++k) {
+    if (warp == 0) {
+      double* part = partials + static_cast<size_t>(k & 1) * nb;
+      int good = 1;
+      if (lane == 0) {
+        if (mode == 1) part[rank] = static_cast<double>(rank + k);
+        good = group_barrier_t0(ctrl, &target, static_cast<unsigned int>(nb), limit_ns, kProbeSite) ? 1 : 0;
+      }
+      good = __shfl_sync(0xffffffffu, good, 0);
+      if (good && mode == 1) {
+        const double sum = fx_warp_sum_array(part, nb);
+        if (lane == 0) total = sum;
+      }
+      if (lane == 0 && !good) ok = 0;
+    }
+    __syncthreads();
+    if (!ok) break;
+    acc += total;
+    __syncthreads();  // total is rewritten by the next sum
+  }
+  if (threadIdx.x == 0) out[rank] = acc;
+}
+
+cudaError_t launch_sync_probe(SolveCtrl* ctrl, double* partials, int iters, int mode, int nblocks,
+                              unsigned long long limit_ns, double* out, cudaStream_t s) {
+  void* args[] = {&ctrl, &partials, &iters, &mode, &limit_ns, &out};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(sync_probe_kernel), dim3(nblocks), dim3(kBlock),
+                                     args, 0, s);
+}
+
 }  // namespace cgk

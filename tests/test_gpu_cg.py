@@ -221,6 +221,17 @@ def test_wait_timeout_selftest_then_context_usable():
     assert res.status == cg.CG_OK
 
 
+def test_group_sync_probe():
+    """The solves' group barrier and group sum timed on the whole grid: both
+    positive and microseconds-scale, a sum (barrier plus publishing and
+    reading the partials) no cheaper than a barrier; bad arguments refused."""
+    cg = cg_mod()
+    bar, summ = cg.cg_probe_group_sync(0, 5000)
+    assert 0.05 < bar < 50.0 and bar <= summ < 100.0, (bar, summ)
+    with pytest.raises(cg.CGError):
+        cg.cg_probe_group_sync(0, 0)
+
+
 @pytest.mark.parametrize("every", [1, 3])
 def test_mixed_frequent_replacement(every):
     """Residual replacement every 1 or 3 steps switches the product between the
