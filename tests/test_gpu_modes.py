@@ -154,18 +154,19 @@ def _hub_matrix(N: int, seed: int):
     return fi.CSR(np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), np.array(va), n)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_large_share_kernel_all_step_kinds(precision):
+@pytest.mark.parametrize("N,precision", [(20, "fp64"), (20, "mixed"), (30, "fp64")])
+def test_large_share_kernel_all_step_kinds(N, precision):
     """The large-share kernel over two CTAs on rows of every step kind at
-    once (up to 9 entries, about 40, about 80, 2,670 and 8,000 entries: one
-    lane, two lanes, a warp per row, and rows spanning several 2,048-entry
-    ring pieces): in FP64 the oracle's iterate at the GPU's step count, in
-    mixed precision the FP64 solution within the residual's reach; the true
-    residual, and the same bits on a second solve."""
+    once (up to 9 entries, about 40, about 80, n/3 and n entries: one lane,
+    two lanes, a warp per row, and rows spanning several 2,048-entry ring
+    pieces; at N = 30 the longest row, 27,000 entries, is longer than the
+    whole 16,384-entry ring): in FP64 the oracle's iterate at the GPU's step
+    count, in mixed precision the FP64 solution within the residual's reach;
+    the true residual, and the same bits on a second solve."""
     cg = cg_mod()
-    A = _hub_matrix(20, 71)
+    A = _hub_matrix(N, 71)
     lens = np.diff(A.row_ptr)
-    assert lens.max() >= 8000 and ((lens > 32) & (lens <= 64)).any() and ((lens > 64) & (lens < 1000)).any()
+    assert lens.max() >= N ** 3 and ((lens > 32) & (lens <= 64)).any() and ((lens > 64) & (lens < 1000)).any()
     b = oracle.spmv(A, fi.xstar(71, A.n))
     mixed = precision == "mixed"
     with handle(A, ctas=2, precision=cg.CG_PREC_MIXED if mixed else cg.CG_PREC_FP64) as h:
