@@ -53,3 +53,42 @@ def kappa_estimate(A, b):
 def iters_close(k_gpu: int, k_orc: int) -> bool:
     """Stopping iterations may differ by rounding of the sums near the threshold."""
     return abs(k_gpu - k_orc) <= max(2, math.ceil(0.01 * k_orc))
+
+
+def hub_matrix(N: int, seed: int):
+    """The 7-point operator on an N^3 grid with coupling rows of three kinds
+    added symmetrically: row 0 coupled to every other row (a row longer than
+    several ring pieces), row n/2 to every third row, 50 rows to 30 random
+    rows each and 50 rows to 70 (rows of about 40 and 80 entries: two-lane
+    and warp steps);
+    each added coupling is -0.01 and adds 0.01 to both diagonals, plus 0.05
+    on every diagonal (strictly diagonally dominant, hence SPD)."""
+    L = fi.laplace7(N)
+    n = L.n
+    rows = [dict(zip(L.col_idx[L.row_ptr[i]:L.row_ptr[i + 1]].tolist(),
+                     L.val[L.row_ptr[i]:L.row_ptr[i + 1]].tolist())) for i in range(n)]
+    rng = np.random.default_rng(seed)
+
+    def couple(i, j):
+        if i == j or j in rows[i]:
+            return
+        rows[i][j] = -0.01
+        rows[j][i] = -0.01
+        rows[i][i] += 0.01
+        rows[j][j] += 0.01
+
+    for j in range(1, n):
+        couple(0, j)
+    for j in range(0, n, 3):
+        couple(n // 2, j)
+    for i in range(100, 200):
+        for j in rng.choice(n, size=30 if i < 150 else 70, replace=False):
+            couple(i, int(j))
+    rp, ci, va = [0], [], []
+    for i in range(n):
+        rows[i][i] += 0.05
+        cols = sorted(rows[i])
+        ci.extend(cols)
+        va.extend(rows[i][c] for c in cols)
+        rp.append(len(ci))
+    return fi.CSR(np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), np.array(va), n)

@@ -14,7 +14,7 @@ import pytest
 
 import fe_inputs as fi
 import oracle
-from gpu_util import cg_mod, iters_close, kappa_estimate
+from gpu_util import cg_mod, hub_matrix, iters_close, kappa_estimate
 
 pytestmark = pytest.mark.gpu
 
@@ -259,6 +259,22 @@ def test_batch_of_256_uneven_systems_sampled():
         A, b = systems[i]
         x = _x(reqs[i])
         assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1.0000001 * TOL
+
+
+@pytest.mark.parametrize("group", [1, 3])
+def test_batch_row_longer_than_the_ring(group):
+    """A system with a row of 27,000 entries (longer than the 16,384-entry
+    shared-memory ring) beside a Q1 system in one batch, on one CTA and on a
+    group of three: every system matches the oracle at equal iterations."""
+    cg = cg_mod()
+    H = hub_matrix(30, 72)
+    systems = [(H, oracle.spmv(H, fi.xstar(72, H.n))), _system(12, 73)]
+    with cg.Batch(group_override=group) as bt:
+        reqs = [_request(A, b, tag=i) for i, (A, b) in enumerate(systems)]
+        res = _wait_all(bt, bt.submit(reqs))
+    for (A, b), req, r in zip(systems, reqs, res):
+        assert r.group == group
+        _check_vs_oracle(A, b, r, _x(req))
 
 
 def test_groups_beyond_one_wave():

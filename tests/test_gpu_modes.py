@@ -8,7 +8,7 @@ import pytest
 
 import fe_inputs as fi
 import oracle
-from gpu_util import cg_mod, handle, iters_close, kappa_estimate
+from gpu_util import cg_mod, handle, hub_matrix, iters_close, kappa_estimate
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -115,45 +115,6 @@ def test_large_share_kernel_neighbour_waits(kind):
     assert np.linalg.norm(x - same.x) <= 1e-8 * np.linalg.norm(same.x)
 
 
-def _hub_matrix(N: int, seed: int):
-    """The 7-point operator on an N^3 grid with coupling rows of three kinds
-    added symmetrically: row 0 coupled to every other row (a row longer than
-    several ring pieces), row n/2 to every third row, 50 rows to 30 random
-    rows each and 50 rows to 70 (rows of about 40 and 80 entries: two-lane
-    and warp steps);
-    each added coupling is -0.01 and adds 0.01 to both diagonals, plus 0.05
-    on every diagonal (strictly diagonally dominant, hence SPD)."""
-    L = fi.laplace7(N)
-    n = L.n
-    rows = [dict(zip(L.col_idx[L.row_ptr[i]:L.row_ptr[i + 1]].tolist(),
-                     L.val[L.row_ptr[i]:L.row_ptr[i + 1]].tolist())) for i in range(n)]
-    rng = np.random.default_rng(seed)
-
-    def couple(i, j):
-        if i == j or j in rows[i]:
-            return
-        rows[i][j] = -0.01
-        rows[j][i] = -0.01
-        rows[i][i] += 0.01
-        rows[j][j] += 0.01
-
-    for j in range(1, n):
-        couple(0, j)
-    for j in range(0, n, 3):
-        couple(n // 2, j)
-    for i in range(100, 200):
-        for j in rng.choice(n, size=30 if i < 150 else 70, replace=False):
-            couple(i, int(j))
-    rp, ci, va = [0], [], []
-    for i in range(n):
-        rows[i][i] += 0.05
-        cols = sorted(rows[i])
-        ci.extend(cols)
-        va.extend(rows[i][c] for c in cols)
-        rp.append(len(ci))
-    return fi.CSR(np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), np.array(va), n)
-
-
 @pytest.mark.parametrize("N,precision", [(20, "fp64"), (20, "mixed"), (30, "fp64")])
 def test_large_share_kernel_all_step_kinds(N, precision):
     """The large-share kernel over two CTAs on rows of every step kind at
@@ -164,7 +125,7 @@ def test_large_share_kernel_all_step_kinds(N, precision):
     count, in mixed precision the FP64 solution within the residual's reach;
     the true residual, and the same bits on a second solve."""
     cg = cg_mod()
-    A = _hub_matrix(N, 71)
+    A = hub_matrix(N, 71)
     lens = np.diff(A.row_ptr)
     assert lens.max() >= N ** 3 and ((lens > 32) & (lens <= 64)).any() and ((lens > 64) & (lens < 1000)).any()
     b = oracle.spmv(A, fi.xstar(71, A.n))
